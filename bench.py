@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused D2Q9/D3Q19 stream-collide hot path.
+
+One benchmark step is one convergence-check interval of the steady-state
+iteration over the whole workload: N-1 fused stream + boundary + collide
+steps, one more that also reduces the FP64 observables, the per-domain
+reduction, and the host readback that the steady-state control needs.  The
+default workload is the Sec. 2 relaxation-time sweep -- 3 resolutions (400x200,
+800x400, 1200x600 at porosities 0.7394 / 0.7532 / 0.7578) x 8 values of tau -
+1/2 -- run as one batch of 24 domains (8.96 M nodes, 0.32 GB per population
+copy, larger than L2).  The metric is MLUPS counted over fluid nodes (million
+fluid-node lattice updates per second), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1609_09685_gb300 import workloads  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS (fluid-node lattice updates/s)"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "small"], default="sweep")
+    p.add_argument("--interval", type=int, default=100)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def get_workload(name: str, rank: int) -> workloads.Workload:
+    if name == "sweep":
+        return workloads.tau_sweep(seed=1 + rank)
+    if name == "batch128":
+        return workloads.batch128(master_seed=2026 + rank)
+    if name == "d3q19":
+        return workloads.d3q19_256(seed=1 + rank)
+    return workloads.small_2d(seed=1 + rank)
+
+
+def lattice_q(wl):
+    return 19 if wl.domains[0].nz > 1 else 9
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+            return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cu", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1609_09685_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, q: int):
+    """DRAM bytes per stream-collide launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        e = d[f"{workload}_q{q}"]
+        if e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (a bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, seconds: float):
+    import oracle as O
+    dom = min(wl.domains, key=lambda d: (d.cells, abs(d.tau - 0.6)))
+    mask, _ = O.qsgs(dom.shape, dom.seed, dom.core_p, dom.porosity, dom.d_face)
+    f = O.init(mask, 1 + dom.drho, 1.0)
+    fluid = int((mask == 0).sum())
+    t0 = time.perf_counter()
+    f = O.run(mask, f, dom.tau, 1 + dom.drho, 1.0, 2)
+    t_probe = (time.perf_counter() - t0) / 2
+    nsteps = max(2, int(seconds / max(t_probe, 1e-6)))
+    t0 = time.perf_counter()
+    O.run(mask, f, dom.tau, 1 + dom.drho, 1.0, nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": fluid * nsteps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, {nsteps} steps of the {dom.nx}x{dom.ny} domain "
+                      f"(tau={dom.tau:.2f}, {fluid} fluid nodes) of the workload, {dt:.1f} s, "
+                      f"single thread"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    wl = get_workload(args.workload, 0)
+    dom = min(wl.domains, key=lambda d: (d.cells, abs(d.tau - 0.6)))
+    mask, _ = O.qsgs(dom.shape, dom.seed, dom.core_p, dom.porosity, dom.d_face)
+    fluid = int((mask == 0).sum())
+    f = O.init(mask, 1 + dom.drho, 1.0)
+    per_step = 4  # oracle time steps per benchmark step (bounded sample)
+    for _ in range(args.warmup):
+        f = O.run(mask, f, dom.tau, 1 + dom.drho, 1.0, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.run(mask, f, dom.tau, 1 + dom.drho, 1.0, per_step)
+    dt = time.perf_counter() - t0
+    v = fluid * per_step * args.steps / dt / 1e6
+    sample = (f"each step = {per_step} FP64 oracle time steps of the {dom.nx}x{dom.ny} domain "
+              f"(tau={dom.tau:.2f}) of workload {wl.name}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+
+    from paper_1609_09685_gb300 import build as B
+    from paper_1609_09685_gb300 import lbm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    lbm.load()
+
+    wl = get_workload(args.workload, rank)
+    q = lattice_q(wl)
+    N = args.interval
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    masks_cache = {}
+    masks = []
+    for d in wl.domains:
+        key = (d.shape, d.seed, d.porosity)
+        if key not in masks_cache:
+            masks_cache[key], _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity, d.d_face, stream=sp)
+        masks.append(masks_cache[key])
+    taus = [d.tau for d in wl.domains]
+    drhos = [d.drho for d in wl.domains]
+    opts = lbm.make_options(stream=sp, check_interval=N)
+    s = lbm.lbm_batch_create(masks, taus, drhos, opts)
+    fluid = s.fluid_nodes
+    bytes_per_launch = 2 * 4 * q * fluid
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lbm.lbm_step(s, N - 1)
+            lbm.lbm_step_observe(s, 1)
+        barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.4)
+        ka = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            ka[k].record(stream)
+            lbm.lbm_step(s, N - 1)
+            kb[k].record(stream)
+            lbm.lbm_step_observe(s, 1)
+        e1.record(stream)
+        barrier()
+        clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    t_kern = sum(a.elapsed_time(b) for a, b in zip(ka, kb)) / 1e3 / (args.steps * (N - 1))
+    updates = float(args.steps * N * fluid)
+    if dist is not None:
+        tt = torch.tensor([t, t_kern], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        uu = torch.tensor([updates], device="cuda", dtype=torch.float64)
+        dist.all_reduce(uu)
+        t, t_kern, updates = float(tt[0]), float(tt[1]), float(uu[0])
+    value = updates / t / 1e6
+
+    # end to end through the C ABI: host masks (pinned) -> create -> one interval
+    # -> permeability back on the host, per step
+    pinned = []
+    for m in masks:
+        pm = torch.empty(m.shape, dtype=torch.uint8, pin_memory=True).numpy()
+        pm[...] = m
+        pinned.append(pm)
+    h2d = sum(m.nbytes for m in pinned) + 48 * len(pinned) + 4 * (len(pinned) + 1)
+    nseg = sum(((d.nx + 31) // 32) * d.ny * d.nz for d in wl.domains)
+    d2h = 4 * nseg + 4 + 8 * lbm.NUM_OBS * len(pinned)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s2 = lbm.lbm_batch_create(pinned, taus, drhos, opts)
+        lbm.lbm_step(s2, N - 1)
+        lbm.lbm_step_observe(s2, 1)
+        k, kn = lbm.lbm_permeability(s2)
+        s2.close()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_updates = float(args.e2e_steps * N * fluid)
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        uu = torch.tensor([e2e_updates], device="cuda", dtype=torch.float64)
+        dist.all_reduce(uu)
+        t_e2e, e2e_updates = float(tt[0]), float(uu[0])
+    s.close()
+
+    if rank == 0:
+        peak, peak_src = measured_hbm_peak()
+        achieved = bytes_per_launch / t_kern / 1e9
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_sample(wl, args.cpu_seconds)
+        total_nodes = wl.cells
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded QSGS masks at the paper's sizes and porosities)",
+            "config": {
+                "workload": wl.name, "domains": len(wl.domains), "lattice": f"D2Q9" if q == 9 else "D3Q19",
+                "nodes": total_nodes, "fluid_nodes": fluid, "check_interval": N,
+                "step": f"{N - 1} fused stream-collide steps + 1 observing step + FP64 reduction + "
+                        "host readback (one convergence-check interval)",
+                "all_node_mlups": value * total_nodes / fluid,
+                "l2": f"inputs larger than L2: {2 * 4 * q * fluid / 1e9:.2f} GB of populations per step",
+                "parallelism": f"independent domains, one replica per GPU ({world})",
+            },
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(args.workload, q),
+                         "kernel": "k_stream_collide", "bytes_per_launch": bytes_per_launch,
+                         "algorithmic_bytes": f"{2 * 4 * q} B per fluid-node update",
+                         "avg_launch_us": t_kern * 1e6, "peak_source": peak_src},
+            "e2e": {"value": e2e_updates / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "step": "create from pinned host masks + one interval + permeability readback"},
+            "gpu_launches": args.steps * (N + 1),
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,893 @@
+// capi.cu -- C ABI and host runtime of the GB300 LBM permeability library.
+//
+// The runtime owns device memory, builds the segment tables, enqueues the
+// kernels of lbm_kernels.cu / qsgs.cu on the solver's stream, captures each
+// convergence-check interval as a CUDA graph, and takes the scalar decisions
+// of the steady-state control (Sec. 2: "iterated to steady state") on the host
+// from the FP64 observables the kernels reduce.  Permeability and Kn follow
+// Sec. 2 (Darcy's law with the mass flow rate; Kn = sqrt(pi/6)(tau-1/2)/N_x)
+// with nu = (tau - 1/2)/3 from Eq. (1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+using namespace lbmgb;
+
+namespace {
+
+thread_local std::string t_err;
+
+struct DomainHost {
+    int32_t nx = 0, ny = 0, nz = 1;
+    double tau = 1.0, drho = 0.0;
+    uint32_t seg_begin = 0, nseg = 0;
+    uint32_t fluid_begin = 0, fluid_count = 0;
+    uint64_t mask_base = 0;
+    int32_t active = 1;
+    lbm_status status = LBM_NOT_CONVERGED;
+    int64_t steps = 0;
+    double residual = INFINITY;
+    std::vector<double> rhist;
+    bool has_obs = false;
+    double obs[kNumObs] = {0};
+};
+
+struct GraphKey {
+    int64_t n;
+    int obs;
+    int parity;
+    bool operator<(const GraphKey& o) const {
+        if (n != o.n) return n < o.n;
+        if (obs != o.obs) return obs < o.obs;
+        return parity < o.parity;
+    }
+};
+
+const char* kVersion = "0.1.0";
+
+}  // namespace
+
+struct lbm_solver {
+    int q = 9, eq = 0;
+    lbm_options opt{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<DomainHost> dom;
+    std::vector<uint8_t> masks;  // concatenated host masks (checkpoint)
+    std::vector<DomainDev> hdom;
+    DomainDev* d_dom = nullptr;
+    uint32_t* d_dom_begin = nullptr;
+    uint32_t* d_seg_dom = nullptr;
+    uint32_t* d_seg_mask = nullptr;
+    uint32_t* d_seg_off = nullptr;
+    uint32_t* d_seg_cnt = nullptr;
+    uint32_t* d_scan = nullptr;
+    uint8_t* d_mask = nullptr;
+    uint32_t nseg_total = 0;
+    uint64_t nfluid = 0, pstride = 0;
+    float* d_g[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* d_uprev = nullptr;
+    double* d_partials = nullptr;
+    double* d_obs = nullptr;
+    double* h_obs = nullptr;  // pinned
+    int64_t step = 0;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err;
+
+    Geometry geom() const {
+        Geometry G;
+        G.dom = d_dom;
+        G.seg_dom = d_seg_dom;
+        G.seg_mask = d_seg_mask;
+        G.seg_off = d_seg_off;
+        G.nseg_total = nseg_total;
+        G.pstride = pstride;
+        return G;
+    }
+};
+
+namespace {
+
+lbm_status fail(lbm_handle h, lbm_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    t_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_handle h, cudaError_t e, const char* what) {
+    const lbm_status s = (e == cudaErrorMemoryAllocation) ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(h, s, m);
+}
+
+#define CK(h, call)                                      \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+void free_solver(lbm_handle h) {
+    if (!h) return;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(h->d_dom);
+    cudaFree(h->d_dom_begin);
+    cudaFree(h->d_seg_dom);
+    cudaFree(h->d_seg_mask);
+    cudaFree(h->d_seg_off);
+    cudaFree(h->d_seg_cnt);
+    cudaFree(h->d_scan);
+    cudaFree(h->d_mask);
+    cudaFree(h->d_g[0]);
+    cudaFree(h->d_g[1]);
+    cudaFree(h->d_uprev);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_obs);
+    if (h->h_obs) cudaFreeHost(h->h_obs);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+double knudsen(double tau, int nx) { return std::sqrt(M_PI / 6.0) * (tau - 0.5) / (double)nx; }
+
+lbm_status upload_dom(lbm_handle h) {
+    for (size_t d = 0; d < h->dom.size(); ++d) h->hdom[d].active = h->dom[d].active;
+    CK(h, cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * h->hdom.size(),
+                          cudaMemcpyHostToDevice, h->st));
+    return LBM_OK;
+}
+
+// Enqueue n steps (the last one observing when obs) plus the reduction and the
+// copy of the observables to pinned host memory.  Advances h->cur.
+lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs) {
+    const Geometry G = h->geom();
+    for (int64_t k = 0; k < n; ++k) {
+        const bool o = obs && (k == n - 1);
+        CK(h, launch_stream_collide(h->q, h->eq, o, G, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
+                                    h->d_partials, h->opt.block_threads, h->st));
+        h->cur ^= 1;
+    }
+    if (obs) {
+        if (n == 0) CK(h, launch_observe(h->q, G, h->d_g[h->cur], h->d_uprev, h->d_partials, h->st));
+        CK(h, launch_reduce_obs(h->d_dom, (int)h->dom.size(), h->d_partials, h->d_obs, h->st));
+        CK(h, cudaMemcpyAsync(h->h_obs, h->d_obs, sizeof(double) * kNumObs * h->dom.size(),
+                              cudaMemcpyDeviceToHost, h->st));
+    }
+    return LBM_OK;
+}
+
+// Same work through a cached CUDA graph (one per step count, observe flag and
+// starting buffer parity).
+lbm_status run_steps(lbm_handle h, int64_t n, bool obs) {
+    if (!h->opt.use_graphs || n <= 1 || h->st == nullptr) return enqueue_steps(h, n, obs);
+    GraphKey key{n, obs ? 1 : 0, h->cur};
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        const int cur0 = h->cur;
+        CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+        lbm_status s = enqueue_steps(h, n, obs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->st, &g);
+        h->cur = cur0;
+        if (s != LBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        it = h->graphs.emplace(key, ex).first;
+    }
+    CK(h, cudaGraphLaunch(it->second, h->st));
+    if (n & 1) h->cur ^= 1;
+    return LBM_OK;
+}
+
+void store_obs(lbm_handle h) {
+    for (size_t d = 0; d < h->dom.size(); ++d) {
+        if (!h->dom[d].active) continue;
+        std::memcpy(h->dom[d].obs, h->h_obs + d * kNumObs, sizeof(double) * kNumObs);
+        h->dom[d].has_obs = true;
+    }
+}
+
+// Copy a retired domain's populations into the other buffer so both hold its
+// final state (no kernel writes a retired domain).
+lbm_status mirror_domain(lbm_handle h, size_t d) {
+    const DomainHost& D = h->dom[d];
+    if (D.fluid_count == 0) return LBM_OK;
+    for (int i = 0; i < h->q; ++i) {
+        const size_t off = (size_t)i * h->pstride + D.fluid_begin;
+        CK(h, cudaMemcpyAsync(h->d_g[h->cur ^ 1] + off, h->d_g[h->cur] + off, sizeof(float) * D.fluid_count,
+                              cudaMemcpyDeviceToDevice, h->st));
+    }
+    return LBM_OK;
+}
+
+lbm_status check_domain(lbm_handle h, int32_t d) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (d < 0 || d >= (int32_t)h->dom.size()) return fail(h, LBM_ERR_ARG, "domain index out of range");
+    return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lbm_version(void) { return kVersion; }
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_NOT_CONVERGED: return "not converged (max_steps reached)";
+        case LBM_STALLED: return "stalled at the FP32 residual floor";
+        case LBM_ERR_ARG: return "invalid argument";
+        case LBM_ERR_CUDA: return "CUDA error";
+        case LBM_ERR_OOM: return "out of device memory";
+        case LBM_DIVERGED: return "diverged (non-finite velocity)";
+        case LBM_TIMEOUT: return "timeout";
+        case LBM_ERR_IO: return "I/O error";
+        case LBM_ERR_INTERNAL: return "internal error";
+        case LBM_CANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : t_err.c_str(); }
+
+void lbm_options_default(lbm_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = (int32_t)sizeof(lbm_options);
+    o->equilibrium = LBM_EQ_QUADRATIC;
+    o->check_interval = 100;
+    o->stall_checks = 20;
+    o->stall_floor = 1e-5;
+    o->rho_out = 1.0;
+    o->stream = nullptr;
+    o->block_threads = 0;
+    o->use_graphs = 1;
+    o->cancel_flag = nullptr;
+}
+
+lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
+                    double d_face, void* stream, uint8_t* mask_out, int32_t* iterations) {
+    if (!mask_out) return fail(nullptr, LBM_ERR_ARG, "mask_out is null");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "sizes must be >= 1");
+    const uint64_t N = (uint64_t)nx * ny * nz;
+    if (N > (1ull << 31)) return fail(nullptr, LBM_ERR_ARG, "more than 2^31 cells");
+    if (!(porosity >= 0.0 && porosity <= 1.0)) return fail(nullptr, LBM_ERR_ARG, "porosity outside [0,1]");
+    if (!(core_p >= 0.0 && core_p <= 1.0) || !(d_face >= 0.0 && d_face <= 1.0))
+        return fail(nullptr, LBM_ERR_ARG, "probabilities outside [0,1]");
+    cudaStream_t st = (cudaStream_t)stream;
+    QsgsScratch sc{};
+    uint8_t* d_mask = nullptr;
+    lbm_status rs = LBM_OK;
+    cudaError_t e = cudaMalloc(&sc.keys, sizeof(uint64_t) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&sc.start, N);
+    if (e == cudaSuccess) e = cudaMalloc(&sc.counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&sc.host_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_mask, N);
+    if (e != cudaSuccess) {
+        rs = cuda_fail(nullptr, e, "qsgs allocation");
+    } else {
+        int it = 0;
+        cudaError_t ce = cudaSuccess;
+        const int r = qsgs_generate(seed, nx, ny, nz, core_p, porosity, d_face, d_mask, sc, st, &it, &ce);
+        if (r == -2) rs = cuda_fail(nullptr, ce, "qsgs kernels");
+        else if (r == -1) rs = fail(nullptr, LBM_ERR_ARG, "bad qsgs arguments");
+        else if (r == -3) rs = fail(nullptr, LBM_ERR_INTERNAL, "no solid core to grow from");
+        else {
+            e = cudaMemcpyAsync(mask_out, d_mask, N, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rs = cuda_fail(nullptr, e, "qsgs copy-out");
+            if (iterations) *iterations = it;
+        }
+    }
+    cudaFree(sc.keys);
+    cudaFree(sc.start);
+    cudaFree(sc.counter);
+    if (sc.host_counter) cudaFreeHost(sc.host_counter);
+    cudaFree(d_mask);
+    return rs;
+}
+
+static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, int force_q,
+                              lbm_handle* out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (n < 1 || !descs) return fail(nullptr, LBM_ERR_ARG, "need at least one domain");
+    lbm_options o;
+    lbm_options_default(&o);
+    if (opt) {
+        if (opt->struct_size != (int32_t)sizeof(lbm_options))
+            return fail(nullptr, LBM_ERR_ARG, "lbm_options.struct_size mismatch");
+        o = *opt;
+    }
+    if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) ||
+        (o.equilibrium != LBM_EQ_QUADRATIC && o.equilibrium != LBM_EQ_LINEAR) || o.block_threads < 0 ||
+        o.block_threads > 1024 || (o.block_threads % 32) != 0)
+        return fail(nullptr, LBM_ERR_ARG, "invalid options");
+    int q = force_q;
+    if (!q) {
+        q = 9;
+        for (int d = 0; d < n; ++d)
+            if (descs[d].nz > 1) q = 19;
+    }
+    uint64_t segs = 0, cells = 0;
+    for (int d = 0; d < n; ++d) {
+        const lbm_domain_desc& D = descs[d];
+        if (!D.mask) return fail(nullptr, LBM_ERR_ARG, "domain mask is null");
+        if (D.nx < 3 || D.ny < 1 || D.nz < 1) return fail(nullptr, LBM_ERR_ARG, "need nx >= 3, ny >= 1, nz >= 1");
+        if (q == 9 && D.nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 domains need nz = 1");
+        if (!(D.tau > 0.5) || !std::isfinite(D.tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be > 0.5");
+        if (!std::isfinite(D.drho) || std::fabs(D.drho) >= o.rho_out)
+            return fail(nullptr, LBM_ERR_ARG, "drho must be finite and |drho| < rho_out");
+        const uint64_t N = (uint64_t)D.nx * D.ny * D.nz;
+        for (uint64_t k = 0; k < N; ++k)
+            if (D.mask[k] > 1) return fail(nullptr, LBM_ERR_ARG, "mask bytes must be 0 (fluid) or 1 (solid)");
+        segs += (uint64_t)((D.nx + kSegW - 1) / kSegW) * D.ny * D.nz;
+        cells += N;
+    }
+    if (segs >= (1ull << 32) || cells >= (1ull << 32)) return fail(nullptr, LBM_ERR_ARG, "batch too large");
+
+    lbm_handle h = new lbm_solver();
+    h->q = q;
+    h->eq = o.equilibrium;
+    h->opt = o;
+    if (o.stream) {
+        h->st = (cudaStream_t)o.stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&h->st);
+        if (e != cudaSuccess) {
+            lbm_status s = cuda_fail(nullptr, e, "cudaStreamCreate");
+            free_solver(h);
+            return s;
+        }
+        h->own_stream = true;
+    }
+    h->dom.resize(n);
+    h->hdom.resize(n);
+    std::vector<uint32_t> begin(n + 1);
+    uint64_t mb = 0;
+    uint32_t sb = 0;
+    for (int d = 0; d < n; ++d) {
+        const lbm_domain_desc& S = descs[d];
+        DomainHost& D = h->dom[d];
+        D.nx = S.nx;
+        D.ny = S.ny;
+        D.nz = S.nz;
+        D.tau = S.tau;
+        D.drho = S.drho;
+        D.seg_begin = sb;
+        D.nseg = (uint32_t)((S.nx + kSegW - 1) / kSegW) * S.ny * S.nz;
+        D.mask_base = mb;
+        begin[d] = sb;
+        DomainDev& G = h->hdom[d];
+        G.nx = S.nx;
+        G.ny = S.ny;
+        G.nz = S.nz;
+        G.nseg = (S.nx + kSegW - 1) / kSegW;
+        G.seg_base = sb;
+        G.nseg_dom = D.nseg;
+        G.omega = (float)(1.0 / S.tau);
+        G.drho_in = (float)S.drho;
+        G.rho0 = (float)o.rho_out;
+        G.active = 1;
+        G.mask_base = mb;
+        const uint64_t N = (uint64_t)S.nx * S.ny * S.nz;
+        h->masks.insert(h->masks.end(), S.mask, S.mask + N);
+        mb += N;
+        sb += D.nseg;
+    }
+    begin[n] = sb;
+    h->nseg_total = sb;
+    *out = h;
+
+#define CKC(call)                                  \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            lbm_status s_ = cuda_fail(nullptr, e_, #call); \
+            free_solver(h);                        \
+            *out = nullptr;                        \
+            return s_;                             \
+        }                                          \
+    } while (0)
+
+    CKC(cudaMalloc(&h->d_dom, sizeof(DomainDev) * n));
+    CKC(cudaMalloc(&h->d_dom_begin, sizeof(uint32_t) * (n + 1)));
+    CKC(cudaMalloc(&h->d_seg_dom, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_seg_mask, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_seg_off, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_seg_cnt, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_scan, sizeof(uint32_t) * ((sb + 1023) / 1024 + 2)));
+    CKC(cudaMalloc(&h->d_mask, std::max<uint64_t>(mb, 1)));
+    CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
+    CKC(cudaMemcpyAsync(h->d_dom_begin, begin.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, h->st));
+    CKC(cudaMemcpyAsync(h->d_mask, h->masks.data(), mb, cudaMemcpyHostToDevice, h->st));
+    const uint32_t nscan = (sb + 1023) / 1024;
+    CKC(launch_seg_setup(h->d_dom, h->d_dom_begin, n, sb, h->d_mask, h->d_seg_dom, h->d_seg_mask, h->d_seg_cnt,
+                         h->d_seg_off, h->d_scan, h->d_scan + nscan + 1, h->st));
+    std::vector<uint32_t> off(sb + 1);
+    uint32_t total = 0;
+    CKC(cudaMemcpyAsync(off.data(), h->d_seg_off, sizeof(uint32_t) * sb, cudaMemcpyDeviceToHost, h->st));
+    CKC(cudaMemcpyAsync(&total, h->d_scan + nscan + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st));
+    CKC(cudaStreamSynchronize(h->st));
+    off[sb] = total;
+    h->nfluid = total;
+    for (int d = 0; d < n; ++d) {
+        h->dom[d].fluid_begin = off[begin[d]];
+        h->dom[d].fluid_count = off[begin[d + 1]] - off[begin[d]];
+    }
+    h->pstride = ((std::max<uint64_t>(total, 1) + 31) / 32) * 32;
+    const int D = (q == 9) ? 2 : 3;
+    CKC(cudaMalloc(&h->d_g[0], sizeof(float) * q * h->pstride));
+    CKC(cudaMalloc(&h->d_g[1], sizeof(float) * q * h->pstride));
+    CKC(cudaMalloc(&h->d_uprev, sizeof(float) * D * h->pstride));
+    CKC(cudaMalloc(&h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_obs, sizeof(double) * kNumObs * n));
+    CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
+    CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));
+    CKC(launch_init(q, h->geom(), h->d_g[0], h->d_uprev, h->st));
+    CKC(cudaStreamSynchronize(h->st));
+#undef CKC
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, lbm_handle* out) {
+    return create_impl(n, descs, opt, 0, out);
+}
+
+lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, double tau, double drho,
+                             const lbm_options* opt, lbm_handle* out) {
+    lbm_domain_desc d{mask, nx, ny, 1, tau, drho};
+    return create_impl(1, &d, opt, 9, out);
+}
+
+lbm_status lbm_create_domain_3d(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, double tau, double drho,
+                                const lbm_options* opt, lbm_handle* out) {
+    lbm_domain_desc d{mask, nx, ny, nz, tau, drho};
+    return create_impl(1, &d, opt, 19, out);
+}
+
+void lbm_destroy(lbm_handle h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    free_solver(h);
+}
+
+lbm_status lbm_info(lbm_handle h, int32_t* n_domains, int32_t* q, int64_t* fluid_nodes_total) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (n_domains) *n_domains = (int32_t)h->dom.size();
+    if (q) *q = h->q;
+    if (fluid_nodes_total) *fluid_nodes_total = (int64_t)h->nfluid;
+    return LBM_OK;
+}
+
+lbm_status lbm_domain_fluid_nodes(lbm_handle h, int32_t d, int64_t* fluid_nodes) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (fluid_nodes) *fluid_nodes = h->dom[d].fluid_count;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    lbm_status s = run_steps(h, nsteps, false);
+    if (s == LBM_OK) {
+        h->step += nsteps;
+        for (auto& D : h->dom)
+            if (D.active) D.has_obs = false;
+    }
+    return s;
+}
+
+lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
+    lbm_status s = run_steps(h, nsteps, true);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->st));
+    h->step += nsteps;
+    store_obs(h);
+    if (obs) std::memcpy(obs, h->h_obs, sizeof(double) * kNumObs * h->dom.size());
+    return LBM_OK;
+}
+
+lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_status* status, int64_t* steps,
+                             double* residual) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (!(tol > 0.0) || max_steps < 0) return fail(h, LBM_ERR_ARG, "need tol > 0 and max_steps >= 0");
+    const size_t n = h->dom.size();
+    for (auto& D : h->dom) {
+        D.active = 1;
+        D.status = LBM_NOT_CONVERGED;
+        D.steps = 0;
+        D.residual = INFINITY;
+        D.rhist.clear();
+    }
+    lbm_status s = upload_dom(h);
+    if (s != LBM_OK) return s;
+    const int64_t N = h->opt.check_interval;
+    int64_t taken = 0;
+    size_t nactive = n;
+    bool cancelled = false;
+    while (nactive > 0 && taken < max_steps) {
+        if (h->opt.cancel_flag && *h->opt.cancel_flag) {
+            cancelled = true;
+            break;
+        }
+        const int64_t k = std::min<int64_t>(N, max_steps - taken);
+        s = run_steps(h, k, true);
+        if (s != LBM_OK) return s;
+        CK(h, cudaStreamSynchronize(h->st));
+        taken += k;
+        h->step += k;
+        store_obs(h);
+        bool retired = false;
+        for (size_t d = 0; d < n; ++d) {
+            DomainHost& D = h->dom[d];
+            if (!D.active) continue;
+            const double* o = D.obs;
+            D.steps = taken;
+            double r;
+            if (o[2] > 0.0) r = std::sqrt(o[1] / o[2]);
+            else r = (o[1] == 0.0) ? 0.0 : INFINITY;
+            D.residual = r;
+            lbm_status ds = LBM_NOT_CONVERGED;
+            if (o[4] > 0.0 || !std::isfinite(o[0])) ds = LBM_DIVERGED;
+            else if (r < tol) ds = LBM_OK;
+            else {
+                D.rhist.push_back(r);
+                const size_t m = D.rhist.size(), w = (size_t)h->opt.stall_checks;
+                if (r < h->opt.stall_floor && m > w && r > 0.9 * D.rhist[m - 1 - w]) ds = LBM_STALLED;
+            }
+            if (ds != LBM_NOT_CONVERGED) {
+                D.status = ds;
+                D.active = 0;
+                --nactive;
+                retired = true;
+                s = mirror_domain(h, d);
+                if (s != LBM_OK) return s;
+            }
+        }
+        if (retired) {
+            s = upload_dom(h);
+            if (s != LBM_OK) return s;
+        }
+    }
+    CK(h, cudaStreamSynchronize(h->st));
+    // leave every domain active for later lbm_step calls
+    bool any_div = false, any_stall = false, any_open = false;
+    for (size_t d = 0; d < n; ++d) {
+        DomainHost& D = h->dom[d];
+        if (D.active) {
+            D.status = cancelled ? LBM_CANCELLED : LBM_NOT_CONVERGED;
+            any_open = true;
+        }
+        any_div |= D.status == LBM_DIVERGED;
+        any_stall |= D.status == LBM_STALLED;
+        if (status) status[d] = D.status;
+        if (steps) steps[d] = D.steps;
+        if (residual) residual[d] = D.residual;
+        D.active = 1;
+    }
+    s = upload_dom(h);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->st));
+    if (cancelled) return fail(h, LBM_CANCELLED, "cancelled by cancel_flag");
+    if (any_div) return fail(h, LBM_DIVERGED, "non-finite velocity in at least one domain");
+    if (any_open) return LBM_NOT_CONVERGED;
+    if (any_stall) return LBM_STALLED;
+    return LBM_OK;
+}
+
+lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (!k) return fail(h, LBM_ERR_ARG, "k is null");
+    bool need = false;
+    for (auto& D : h->dom) need |= !D.has_obs;
+    if (need) {
+        // observe the current state (this also refreshes u_prev)
+        lbm_status s = enqueue_steps(h, 0, true);
+        if (s != LBM_OK) return s;
+        CK(h, cudaStreamSynchronize(h->st));
+        store_obs(h);
+    }
+    lbm_status rs = LBM_OK;
+    for (size_t d = 0; d < h->dom.size(); ++d) {
+        const DomainHost& D = h->dom[d];
+        const double nu = (D.tau - 0.5) / 3.0;
+        const double jmean = D.obs[0] / ((double)D.nx * D.ny * D.nz);
+        if (D.drho == 0.0) {
+            k[d] = NAN;
+            rs = fail(h, LBM_ERR_ARG, "drho = 0: permeability undefined");
+        } else {
+            k[d] = nu * jmean * (double)(D.nx - 1) / ((1.0 / 3.0) * D.drho);
+        }
+        if (kn) kn[d] = knudsen(D.tau, D.nx);
+    }
+    return rs;
+}
+
+lbm_status lbm_get_fields(lbm_handle h, int32_t d, double* rho, double* ux, double* uy, double* uz) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!rho || !ux || !uy || (h->q == 19 && !uz)) return fail(h, LBM_ERR_ARG, "null output");
+    const DomainHost& D = h->dom[d];
+    const size_t N = (size_t)D.nx * D.ny * D.nz;
+    double* buf = nullptr;
+    CK(h, cudaMalloc(&buf, sizeof(double) * N * 4));
+    const cudaError_t e1 = launch_export_fields(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out,
+                                                h->d_g[h->cur], buf, buf + N, buf + 2 * N,
+                                                h->q == 19 ? buf + 3 * N : nullptr, h->st);
+    cudaError_t e = e1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rho, buf, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ux, buf + N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(uy, buf + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h->q == 19)
+        e = cudaMemcpyAsync(uz, buf + 3 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_fields");
+    if (h->q == 9 && uz) std::memset(uz, 0, sizeof(double) * N);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_handle h, int32_t d, double* f) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(h, LBM_ERR_ARG, "null output");
+    const DomainHost& D = h->dom[d];
+    const size_t M = (size_t)D.nx * D.ny * D.nz * h->q;
+    double* buf = nullptr;
+    CK(h, cudaMalloc(&buf, sizeof(double) * M));
+    cudaError_t e = launch_export_pops(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out, h->d_g[h->cur],
+                                       buf, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, buf, sizeof(double) * M, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_populations");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle h, int32_t d, const double* f) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(h, LBM_ERR_ARG, "null input");
+    const DomainHost& D = h->dom[d];
+    const size_t M = (size_t)D.nx * D.ny * D.nz * h->q;
+    double* buf = nullptr;
+    CK(h, cudaMalloc(&buf, sizeof(double) * M));
+    cudaError_t e = cudaMemcpyAsync(buf, f, sizeof(double) * M, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+        e = launch_import_pops(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out, buf, h->d_g[h->cur], h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_populations");
+    h->dom[d].has_obs = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const float* ux, const float* uy,
+                          const float* uz, int32_t on_device) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!drho || !ux || !uy || (h->q == 19 && !uz)) return fail(h, LBM_ERR_ARG, "null input");
+    const DomainHost& D = h->dom[d];
+    const size_t N = (size_t)D.nx * D.ny * D.nz;
+    float* buf = nullptr;
+    const float *a = drho, *b = ux, *c = uy, *z = (h->q == 19) ? uz : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        CK(h, cudaMalloc(&buf, sizeof(float) * N * 4));
+        e = cudaMemcpyAsync(buf, drho, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf + N, ux, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 2 * N, uy, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess && z)
+            e = cudaMemcpyAsync(buf + 3 * N, uz, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
+        a = buf;
+        b = buf + N;
+        c = buf + 2 * N;
+        z = z ? buf + 3 * N : nullptr;
+    }
+    if (e == cudaSuccess)
+        e = launch_set_fields(h->q, h->eq, h->geom(), D.seg_begin, D.nseg, a, b, c, z, h->d_g[h->cur],
+                              h->d_uprev, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
+    h->dom[d].has_obs = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_step(lbm_handle h, int64_t* step) {
+    if (!h || !step) return fail(h, LBM_ERR_ARG, "null argument");
+    *step = h->step;
+    return LBM_OK;
+}
+
+// Checkpoint layout: magic, version, header ints, per-domain records, masks,
+// then per domain its compact populations (Q planes) and u_prev (D planes).
+static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+
+lbm_status lbm_save(lbm_handle h, const char* path) {
+    if (!h || !path) return fail(h, LBM_ERR_ARG, "null argument");
+    CK(h, cudaStreamSynchronize(h->st));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(h, LBM_ERR_IO, std::string("cannot open ") + path);
+    const int D = (h->q == 9) ? 2 : 3;
+    bool ok = true;
+    auto W = [&](const void* p, size_t sz) { ok = ok && std::fwrite(p, 1, sz, fp) == sz; };
+    const int32_t hdr[4] = {1, h->q, h->eq, (int32_t)h->dom.size()};
+    W(kMagic, 8);
+    W(hdr, sizeof(hdr));
+    W(&h->step, sizeof(h->step));
+    W(&h->opt.rho_out, sizeof(double));
+    for (const DomainHost& d : h->dom) {
+        const int32_t dims[3] = {d.nx, d.ny, d.nz};
+        W(dims, sizeof(dims));
+        W(&d.tau, sizeof(double));
+        W(&d.drho, sizeof(double));
+        const int32_t st = (int32_t)d.status;
+        W(&st, sizeof(st));
+        W(&d.steps, sizeof(d.steps));
+        W(&d.residual, sizeof(double));
+        const int32_t ho = d.has_obs ? 1 : 0;
+        W(&ho, sizeof(ho));
+        W(d.obs, sizeof(d.obs));
+    }
+    W(h->masks.data(), h->masks.size());
+    std::vector<float> tmp;
+    for (const DomainHost& d : h->dom) {
+        tmp.resize((size_t)d.fluid_count);
+        for (int i = 0; i < h->q + D && ok; ++i) {
+            const float* src = (i < h->q) ? h->d_g[h->cur] + (size_t)i * h->pstride
+                                          : h->d_uprev + (size_t)(i - h->q) * h->pstride;
+            if (d.fluid_count) {
+                cudaError_t e = cudaMemcpy(tmp.data(), src + d.fluid_begin, sizeof(float) * d.fluid_count,
+                                           cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) {
+                    std::fclose(fp);
+                    return cuda_fail(h, e, "lbm_save copy");
+                }
+            }
+            W(tmp.data(), sizeof(float) * tmp.size());
+        }
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(h, LBM_ERR_IO, "write failed");
+    return LBM_OK;
+}
+
+lbm_status lbm_load(const char* path, const lbm_options* opt, lbm_handle* out) {
+    if (!path || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(nullptr, LBM_ERR_IO, std::string("cannot open ") + path);
+    bool ok = true;
+    auto R = [&](void* p, size_t sz) { ok = ok && std::fread(p, 1, sz, fp) == sz; };
+    char magic[8];
+    int32_t hdr[4];
+    int64_t step = 0;
+    double rho_out = 1.0;
+    R(magic, 8);
+    R(hdr, sizeof(hdr));
+    R(&step, sizeof(step));
+    R(&rho_out, sizeof(double));
+    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || hdr[0] != 1 || (hdr[1] != 9 && hdr[1] != 19) || hdr[3] < 1 ||
+        hdr[3] > (1 << 24)) {
+        std::fclose(fp);
+        return fail(nullptr, LBM_ERR_IO, "not a checkpoint of this library version");
+    }
+    const int n = hdr[3];
+    struct Rec {
+        int32_t dims[3];
+        double tau, drho;
+        int32_t st;
+        int64_t steps;
+        double residual;
+        int32_t has_obs;
+        double obs[kNumObs];
+    };
+    std::vector<Rec> recs(n);
+    uint64_t cells = 0;
+    for (int d = 0; d < n && ok; ++d) {
+        Rec& r = recs[d];
+        R(r.dims, sizeof(r.dims));
+        R(&r.tau, sizeof(double));
+        R(&r.drho, sizeof(double));
+        R(&r.st, sizeof(int32_t));
+        R(&r.steps, sizeof(int64_t));
+        R(&r.residual, sizeof(double));
+        R(&r.has_obs, sizeof(int32_t));
+        R(r.obs, sizeof(r.obs));
+        if (r.dims[0] < 3 || r.dims[1] < 1 || r.dims[2] < 1 || r.dims[0] > (1 << 20) || r.dims[1] > (1 << 20) ||
+            r.dims[2] > (1 << 20))
+            ok = false;
+        else
+            cells += (uint64_t)r.dims[0] * r.dims[1] * r.dims[2];
+    }
+    if (!ok || cells >= (1ull << 32)) {
+        std::fclose(fp);
+        return fail(nullptr, LBM_ERR_IO, "truncated or corrupt checkpoint header");
+    }
+    std::vector<uint8_t> masks(cells);
+    R(masks.data(), cells);
+    if (!ok) {
+        std::fclose(fp);
+        return fail(nullptr, LBM_ERR_IO, "truncated checkpoint (masks)");
+    }
+    lbm_options o;
+    lbm_options_default(&o);
+    if (opt) o = *opt;
+    o.equilibrium = hdr[2];
+    o.rho_out = rho_out;
+    std::vector<lbm_domain_desc> descs(n);
+    uint64_t mb = 0;
+    for (int d = 0; d < n; ++d) {
+        descs[d] = lbm_domain_desc{masks.data() + mb, recs[d].dims[0], recs[d].dims[1], recs[d].dims[2],
+                                   recs[d].tau, recs[d].drho};
+        mb += (uint64_t)recs[d].dims[0] * recs[d].dims[1] * recs[d].dims[2];
+    }
+    lbm_handle h = nullptr;
+    lbm_status s = create_impl(n, descs.data(), &o, hdr[1], &h);
+    if (s != LBM_OK) {
+        std::fclose(fp);
+        return s;
+    }
+    const int D = (h->q == 9) ? 2 : 3;
+    std::vector<float> tmp;
+    for (int d = 0; d < n && ok; ++d) {
+        DomainHost& dh = h->dom[d];
+        tmp.resize((size_t)dh.fluid_count);
+        for (int i = 0; i < h->q + D && ok; ++i) {
+            R(tmp.data(), sizeof(float) * tmp.size());
+            if (!ok) break;
+            float* dst = (i < h->q) ? h->d_g[0] + (size_t)i * h->pstride : h->d_uprev + (size_t)(i - h->q) * h->pstride;
+            if (dh.fluid_count) {
+                cudaError_t e = cudaMemcpy(dst + dh.fluid_begin, tmp.data(), sizeof(float) * dh.fluid_count,
+                                           cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    std::fclose(fp);
+                    lbm_status cs = cuda_fail(nullptr, e, "lbm_load copy");
+                    free_solver(h);
+                    return cs;
+                }
+            }
+        }
+        dh.status = (lbm_status)recs[d].st;
+        dh.steps = recs[d].steps;
+        dh.residual = recs[d].residual;
+        dh.has_obs = recs[d].has_obs != 0;
+        std::memcpy(dh.obs, recs[d].obs, sizeof(dh.obs));
+    }
+    std::fclose(fp);
+    if (!ok) {
+        free_solver(h);
+        return fail(nullptr, LBM_ERR_IO, "truncated checkpoint (populations)");
+    }
+    h->cur = 0;
+    h->step = step;
+    *out = h;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// lbm_device.cuh -- device-side types and lattice traits of the GB300 LBM
+// library (shared by the library's own .cu files only).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace lbmgb {
+
+constexpr int kNumObs = 8;  // per-domain observables, see lbm.h lbm_step_observe
+constexpr int kSegW = 32;   // nodes per segment (one warp lane per node)
+
+// Velocity sets of Qian, d'Humieres & Lallemand (1992), in the order that
+// include/lbm.h documents.  Components are looked up with compile-time
+// indices after loop unrolling, so every table access folds to a constant.
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr int D = 2;
+    static constexpr int NROW = 3;  // neighbour rows (dy in -1..1)
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double wd(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19;
+    static constexpr int D = 3;
+    static constexpr int NROW = 9;  // neighbour rows (dy, dz in -1..1)
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                  {0, 0, 1},   {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double wd(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// Direction with velocity (x, y, z); -1 when absent.
+template <class L>
+__host__ __device__ constexpr int find_dir(int x, int y, int z) {
+    for (int j = 0; j < L::Q; ++j)
+        if (L::c(j, 0) == x && L::c(j, 1) == y && L::c(j, 2) == z) return j;
+    return -1;
+}
+template <class L>
+__host__ __device__ constexpr int opp(int i) {
+    return find_dir<L>(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+}
+// Direction i with its y (and/or z) component reversed: specular reflection.
+template <class L>
+__host__ __device__ constexpr int flip(int i, bool fy, bool fz) {
+    return find_dir<L>(L::c(i, 0), fy ? -L::c(i, 1) : L::c(i, 1), fz ? -L::c(i, 2) : L::c(i, 2));
+}
+
+// One domain of a batch as the kernels see it.
+struct DomainDev {
+    int32_t nx, ny, nz;  // nz = 1 in 2D
+    int32_t nseg;        // segments per x-row, ceil(nx / 32)
+    uint32_t seg_base;   // first global segment of the domain
+    uint32_t nseg_dom;   // nseg * ny * nz
+    float omega;         // 1 / tau
+    float drho_in;       // rho_in - rho_0 (outlet carries rho_0 exactly)
+    float rho0;          // rho_0 = rho_out
+    int32_t active;      // 0 once retired by the steady-state control
+    uint64_t mask_base;  // byte offset of the domain's dense mask
+};
+
+// Arguments shared by every segment kernel.
+struct Geometry {
+    const DomainDev* dom;
+    const uint32_t* seg_dom;   // domain of each global segment
+    const uint32_t* seg_mask;  // fluid bits of each segment (bit l = node x = 32 s + l)
+    const uint32_t* seg_off;   // compact index of the segment's first fluid node
+    uint32_t nseg_total;
+    uint64_t pstride;  // elements between direction planes of a population array
+};
+
+}  // namespace lbmgb

@@ -1,0 +1,46 @@
+// lbm_launch.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbm_device.cuh"
+
+namespace lbmgb {
+
+cudaError_t launch_stream_collide(int q, int eq, bool obs, const Geometry& G, const float* src,
+                                  float* dst, float* uprev, double* partials, int threads,
+                                  cudaStream_t st);
+cudaError_t launch_observe(int q, const Geometry& G, const float* g, float* uprev, double* partials,
+                           cudaStream_t st);
+cudaError_t launch_reduce_obs(const DomainDev* dom, int ndom, const double* partials, double* obs,
+                              cudaStream_t st);
+cudaError_t launch_init(int q, const Geometry& G, float* g, float* uprev, cudaStream_t st);
+cudaError_t launch_export_pops(int q, const Geometry& G, uint32_t base, uint32_t nseg, double rho0,
+                               const float* g, double* out, cudaStream_t st);
+cudaError_t launch_import_pops(int q, const Geometry& G, uint32_t base, uint32_t nseg, double rho0,
+                               const double* in, float* g, cudaStream_t st);
+cudaError_t launch_export_fields(int q, const Geometry& G, uint32_t base, uint32_t nseg, double rho0,
+                                 const float* g, double* rho, double* ux, double* uy, double* uz,
+                                 cudaStream_t st);
+cudaError_t launch_set_fields(int q, int eq, const Geometry& G, uint32_t base, uint32_t nseg,
+                              const float* drho, const float* ux, const float* uy, const float* uz,
+                              float* g, float* uprev, cudaStream_t st);
+cudaError_t launch_seg_setup(const DomainDev* dom, const uint32_t* dom_begin, int ndom,
+                             uint32_t nseg_total, const uint8_t* mask, uint32_t* seg_dom,
+                             uint32_t* seg_mask, uint32_t* seg_cnt, uint32_t* seg_off,
+                             uint32_t* scan_totals, uint32_t* grand_total, cudaStream_t st);
+
+// QSGS (qsgs.cu).  keys: N uint64 scratch; counter: one uint64 scratch.
+struct QsgsScratch {
+    uint64_t* keys;
+    uint8_t* start;
+    unsigned long long* counter;
+    unsigned long long* host_counter;  // pinned
+};
+// Returns 0 on success, -1 argument error, -3 no cores, -2 CUDA error (cuda_err set).
+int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double porosity,
+                  double d_face, uint8_t* d_mask, const QsgsScratch& sc, cudaStream_t st,
+                  int* iterations, cudaError_t* cuda_err);
+
+}  // namespace lbmgb

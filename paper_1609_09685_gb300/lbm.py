@@ -1,0 +1,349 @@
+"""Thin ctypes binding of ``include/lbm.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of the method: numpy arrays are passed as host pointers, results
+are copied back, and a non-OK status raises :class:`LBMError`.  The CUDA
+library must have been built (``python -m paper_1609_09685_gb300.build``);
+importing the binding without it fails loudly.  PyTorch supplies only the CUDA
+stream (``torch.cuda.current_stream()``) when the caller asks for it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_NOT_CONVERGED = 1
+LBM_STALLED = 2
+LBM_ERR_ARG = -1
+LBM_ERR_CUDA = -2
+LBM_ERR_OOM = -3
+LBM_DIVERGED = -4
+LBM_TIMEOUT = -5
+LBM_ERR_IO = -6
+LBM_ERR_INTERNAL = -7
+LBM_CANCELLED = -8
+LBM_EQ_QUADRATIC = 0
+LBM_EQ_LINEAR = 1
+NUM_OBS = 8
+
+# informational statuses that do not raise
+_SOFT = (LBM_OK, LBM_NOT_CONVERGED, LBM_STALLED)
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class lbm_options(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_int32),
+        ("equilibrium", C.c_int32),
+        ("check_interval", C.c_int32),
+        ("stall_checks", C.c_int32),
+        ("stall_floor", C.c_double),
+        ("rho_out", C.c_double),
+        ("stream", C.c_void_p),
+        ("block_threads", C.c_int32),
+        ("use_graphs", C.c_int32),
+        ("cancel_flag", C.c_void_p),
+    ]
+
+
+class lbm_domain_desc(C.Structure):
+    _fields_ = [
+        ("mask", C.c_void_p),
+        ("nx", C.c_int32),
+        ("ny", C.c_int32),
+        ("nz", C.c_int32),
+        ("tau", C.c_double),
+        ("drho", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"CUDA library {p} is missing: build it with `python -m paper_1609_09685_gb300.build`")
+    lib = C.CDLL(p)
+    P, i32, i64, d, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint64
+    sigs = {
+        "lbm_version": (C.c_char_p, []),
+        "lbm_status_string": (C.c_char_p, [i32]),
+        "lbm_last_error": (C.c_char_p, [P]),
+        "lbm_options_default": (None, [P]),
+        "lbm_qsgs": (i32, [u64, i32, i32, i32, d, d, d, P, P, P]),
+        "lbm_batch_create": (i32, [i32, P, P, P]),
+        "lbm_create_domain": (i32, [P, i32, i32, d, d, P, P]),
+        "lbm_create_domain_3d": (i32, [P, i32, i32, i32, d, d, P, P]),
+        "lbm_destroy": (None, [P]),
+        "lbm_info": (i32, [P, P, P, P]),
+        "lbm_domain_fluid_nodes": (i32, [P, i32, P]),
+        "lbm_step": (i32, [P, i64]),
+        "lbm_step_observe": (i32, [P, i64, P]),
+        "lbm_run_to_steady": (i32, [P, d, i64, P, P, P]),
+        "lbm_permeability": (i32, [P, P, P]),
+        "lbm_get_fields": (i32, [P, i32, P, P, P, P]),
+        "lbm_get_populations": (i32, [P, i32, P]),
+        "lbm_set_populations": (i32, [P, i32, P]),
+        "lbm_set_fields": (i32, [P, i32, P, P, P, P, i32]),
+        "lbm_get_step": (i32, [P, P]),
+        "lbm_save": (i32, [P, C.c_char_p]),
+        "lbm_load": (i32, [C.c_char_p, P, P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, handle=None, soft=_SOFT) -> int:
+    if st in soft:
+        return st
+    msg = load().lbm_last_error(handle).decode(errors="replace")
+    raise LBMError(st, msg or load().lbm_status_string(st).decode())
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def current_stream() -> Optional[int]:
+    """torch's current CUDA stream handle, or None."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=20,
+                 stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
+                 use_graphs=True, cancel_flag=None) -> lbm_options:
+    o = lbm_options()
+    load().lbm_options_default(C.byref(o))
+    o.equilibrium = equilibrium
+    o.check_interval = check_interval
+    o.stall_checks = stall_checks
+    o.stall_floor = stall_floor
+    o.rho_out = rho_out
+    o.stream = stream
+    o.block_threads = block_threads
+    o.use_graphs = 1 if use_graphs else 0
+    o.cancel_flag = cancel_flag
+    return o
+
+
+def _mask(m) -> np.ndarray:
+    a = np.ascontiguousarray(m, dtype=np.uint8)
+    if a.ndim not in (2, 3):
+        raise ValueError("mask must be [ny, nx] or [nz, ny, nx]")
+    return a
+
+
+def lbm_version() -> str:
+    return load().lbm_version().decode()
+
+
+def lbm_qsgs(seed: int, shape: Sequence[int], core_p: float, porosity: float,
+             d_face: float = 0.2, stream=None):
+    """QSGS mask (uint8, shape (ny, nx) or (nz, ny, nx)) and iteration count."""
+    if len(shape) == 2:
+        nz, (ny, nx) = 1, shape
+    else:
+        nz, ny, nx = shape
+    out = np.zeros((nz, ny, nx), np.uint8)
+    it = C.c_int32(0)
+    _check(load().lbm_qsgs(seed & (2**64 - 1), nx, ny, nz, core_p, porosity, d_face, stream,
+                           _ptr(out), C.byref(it)))
+    return (out[0] if len(shape) == 2 else out), it.value
+
+
+class Solver:
+    """Owner of an ``lbm_handle`` (a batch of one or more domains)."""
+
+    def __init__(self, handle: C.c_void_p, masks, taus, drhos, options: lbm_options):
+        self._h = handle
+        self.masks = masks
+        self.taus = list(taus)
+        self.drhos = list(drhos)
+        self.options = options
+        n, q, nf = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(load().lbm_info(self._h, C.byref(n), C.byref(q), C.byref(nf)), self._h)
+        self.n_domains, self.q, self.fluid_nodes = n.value, q.value, nf.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def lbm_batch_create(masks: Sequence[np.ndarray], taus: Sequence[float], drhos: Sequence[float],
+                     options: Optional[lbm_options] = None) -> Solver:
+    masks = [_mask(m) for m in masks]
+    n = len(masks)
+    descs = (lbm_domain_desc * n)()
+    for k, m in enumerate(masks):
+        if m.ndim == 2:
+            nz, (ny, nx) = 1, m.shape
+        else:
+            nz, ny, nx = m.shape
+        descs[k] = lbm_domain_desc(m.ctypes.data, nx, ny, nz, float(taus[k]), float(drhos[k]))
+    o = options or make_options()
+    h = C.c_void_p()
+    _check(load().lbm_batch_create(n, descs, C.byref(o), C.byref(h)))
+    return Solver(h, masks, taus, drhos, o)
+
+
+def lbm_create_domain(mask, tau: float, drho: float, options: Optional[lbm_options] = None) -> Solver:
+    m = _mask(mask)
+    if m.ndim != 2:
+        raise ValueError("lbm_create_domain takes a 2D mask; use lbm_create_domain_3d")
+    o = options or make_options()
+    h = C.c_void_p()
+    _check(load().lbm_create_domain(_ptr(m), m.shape[1], m.shape[0], tau, drho, C.byref(o),
+                                    C.byref(h)))
+    return Solver(h, [m], [tau], [drho], o)
+
+
+def lbm_create_domain_3d(mask, tau: float, drho: float,
+                         options: Optional[lbm_options] = None) -> Solver:
+    m = _mask(mask)
+    if m.ndim != 3:
+        raise ValueError("lbm_create_domain_3d takes a [nz, ny, nx] mask")
+    o = options or make_options()
+    h = C.c_void_p()
+    nz, ny, nx = m.shape
+    _check(load().lbm_create_domain_3d(_ptr(m), nx, ny, nz, tau, drho, C.byref(o), C.byref(h)))
+    return Solver(h, [m], [tau], [drho], o)
+
+
+def lbm_domain_fluid_nodes(s: Solver, d: int) -> int:
+    v = C.c_int64()
+    _check(load().lbm_domain_fluid_nodes(s.handle, d, C.byref(v)), s.handle)
+    return v.value
+
+
+def lbm_step(s: Solver, nsteps: int) -> None:
+    _check(load().lbm_step(s.handle, int(nsteps)), s.handle)
+
+
+def lbm_step_observe(s: Solver, nsteps: int) -> np.ndarray:
+    out = np.zeros((s.n_domains, NUM_OBS), np.float64)
+    _check(load().lbm_step_observe(s.handle, int(nsteps), _ptr(out)), s.handle)
+    return out
+
+
+def lbm_run_to_steady(s: Solver, tol: float, max_steps: int):
+    """Returns (overall status, per-domain status, steps, residual)."""
+    n = s.n_domains
+    st = np.zeros(n, np.int32)
+    steps = np.zeros(n, np.int64)
+    res = np.zeros(n, np.float64)
+    rc = _check(load().lbm_run_to_steady(s.handle, tol, int(max_steps), _ptr(st), _ptr(steps),
+                                         _ptr(res)), s.handle)
+    return rc, st, steps, res
+
+
+def lbm_permeability(s: Solver):
+    """(k[n], kn[n]) from the last observation."""
+    k = np.zeros(s.n_domains, np.float64)
+    kn = np.zeros(s.n_domains, np.float64)
+    _check(load().lbm_permeability(s.handle, _ptr(k), _ptr(kn)), s.handle)
+    return k, kn
+
+
+def _shape(s: Solver, d: int):
+    return s.masks[d].shape
+
+
+def lbm_get_fields(s: Solver, d: int = 0):
+    shp = _shape(s, d)
+    arrs = [np.zeros(shp, np.float64) for _ in range(4)]
+    _check(load().lbm_get_fields(s.handle, d, *[_ptr(a) for a in arrs]), s.handle)
+    return tuple(arrs[:3] if s.q == 9 else arrs)
+
+
+def lbm_get_populations(s: Solver, d: int = 0) -> np.ndarray:
+    f = np.zeros(_shape(s, d) + (s.q,), np.float64)
+    _check(load().lbm_get_populations(s.handle, d, _ptr(f)), s.handle)
+    return f
+
+
+def lbm_set_populations(s: Solver, d: int, f: np.ndarray) -> None:
+    a = np.ascontiguousarray(f, np.float64)
+    if a.shape != _shape(s, d) + (s.q,):
+        raise ValueError(f"expected shape {_shape(s, d) + (s.q,)}")
+    _check(load().lbm_set_populations(s.handle, d, _ptr(a)), s.handle)
+
+
+def lbm_set_fields(s: Solver, d: int, drho, ux, uy, uz=None, on_device: bool = False) -> None:
+    """Warm start from dense float32 fields (numpy arrays, or device pointers /
+    torch CUDA tensors with on_device=True)."""
+    if on_device:
+        ptrs = [C.c_void_p(int(a.data_ptr()) if hasattr(a, "data_ptr") else int(a)) if a is not None
+                else None for a in (drho, ux, uy, uz)]
+        _check(load().lbm_set_fields(s.handle, d, *ptrs, 1), s.handle)
+        return
+    arrs = [None if a is None else np.ascontiguousarray(a, np.float32) for a in (drho, ux, uy, uz)]
+    for a in arrs:
+        if a is not None and a.shape != _shape(s, d):
+            raise ValueError("field shape mismatch")
+    _check(load().lbm_set_fields(s.handle, d, *[None if a is None else _ptr(a) for a in arrs], 0),
+           s.handle)
+
+
+def lbm_get_step(s: Solver) -> int:
+    v = C.c_int64()
+    _check(load().lbm_get_step(s.handle, C.byref(v)), s.handle)
+    return v.value
+
+
+def lbm_save(s: Solver, path: str) -> None:
+    _check(load().lbm_save(s.handle, path.encode()), s.handle)
+
+
+def lbm_load(path: str, masks=None, options: Optional[lbm_options] = None) -> Solver:
+    o = options or make_options()
+    h = C.c_void_p()
+    _check(load().lbm_load(path.encode(), C.byref(o), C.byref(h)))
+    return Solver(h, masks if masks is not None else [], [], [], o)

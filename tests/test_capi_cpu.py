@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads and exports every entry point of
+include/lbm.h; argument validation happens before any device work, so it is
+checked here without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1609_09685_gb300 import build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    names = _declared()
+    for n in ("lbm_qsgs", "lbm_create_domain", "lbm_create_domain_3d", "lbm_batch_create",
+              "lbm_run_to_steady", "lbm_permeability", "lbm_step", "lbm_get_fields",
+              "lbm_get_populations", "lbm_set_populations", "lbm_set_fields", "lbm_save",
+              "lbm_load"):
+        assert n in names
+        assert hasattr(lbm, n)
+
+
+def test_version_and_status_strings(lib):
+    assert re.match(r"\d+\.\d+\.\d+", lbm.lbm_version())
+    assert lib.lbm_status_string(lbm.LBM_ERR_ARG).decode() == "invalid argument"
+
+
+def _create_status(mask, tau=0.8, drho=1e-3):
+    o = lbm.make_options()
+    h = C.c_void_p()
+    m = np.ascontiguousarray(mask, np.uint8)
+    return lbm.load().lbm_create_domain(m.ctypes.data, m.shape[1], m.shape[0], tau, drho,
+                                        C.byref(o), C.byref(h)), h
+
+
+@pytest.mark.parametrize("kw,shape", [
+    (dict(tau=0.5), (8, 8)),          # tau must exceed 1/2
+    (dict(tau=float("nan")), (8, 8)),
+    (dict(drho=float("inf")), (8, 8)),
+    (dict(), (8, 2)),                 # nx < 3
+])
+def test_create_rejects_bad_arguments(lib, kw, shape):
+    st, h = _create_status(np.zeros(shape), **kw)
+    assert st == lbm.LBM_ERR_ARG
+    assert h.value is None
+    assert lib.lbm_last_error(None).decode()
+
+
+def test_create_rejects_non_binary_mask(lib):
+    m = np.zeros((6, 9), np.uint8)
+    m[2, 3] = 7
+    st, _ = _create_status(m)
+    assert st == lbm.LBM_ERR_ARG
+    assert "0 (fluid) or 1 (solid)" in lib.lbm_last_error(None).decode()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_run_to_steady(None, 1e-9, 10, None, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_permeability(None, None, None) == lbm.LBM_ERR_ARG
+
+
+def test_qsgs_rejects_bad_arguments(lib):
+    out = np.zeros(16, np.uint8)
+    assert lib.lbm_qsgs(1, 4, 4, 1, 0.02, 1.5, 0.2, None, out.ctypes.data, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_qsgs(1, 0, 4, 1, 0.02, 0.5, 0.2, None, out.ctypes.data, None) == lbm.LBM_ERR_ARG
+
+
+def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
+    h = C.c_void_p()
+    o = lbm.make_options()
+    assert lib.lbm_load(str(tmp_path / "nope").encode(), C.byref(o), C.byref(h)) == lbm.LBM_ERR_IO
+    p = tmp_path / "bad.ckpt"
+    p.write_bytes(b"LBMGB300" + b"\x00" * 7)
+    assert lib.lbm_load(str(p).encode(), C.byref(o), C.byref(h)) == lbm.LBM_ERR_IO

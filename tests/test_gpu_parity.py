@@ -1,0 +1,278 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances.  The device state is FP32 shifted populations g = f - w rho_0.
+One step of stream + boundary + collide is a few dozen FP32 operations on
+values of magnitude max|g|, so one step's rounding is a few ulp of max|g|
+(2^-24 ~ 6e-8 relative); over up to 10 steps the errors add, not multiply
+(the BGK update is a contraction for tau > 1/2).  The bound used is
+    |g_gpu - g_oracle| <= 2e-6 max|g_oracle|,
+i.e. ~30 ulp of the largest population.  Converged permeabilities must agree
+to 1e-4 relative and velocity fields to 1e-3 relative L2.
+QSGS masks, segment tables and statuses are integer work and must match
+exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1609_09685_gb300 import build, lbm, workloads
+
+pytestmark = pytest.mark.gpu
+
+REL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    lbm.load()
+    O.build()
+
+
+def _w(q):
+    return O.lattice(q)[1]
+
+
+def _shifted(f, q, rho0=1.0):
+    return f - _w(q) * rho0
+
+
+def _assert_close(gpu_f, orc_f, q, mask, rel=REL):
+    fluid = ~mask.astype(bool)
+    a = _shifted(gpu_f, q)[fluid]
+    b = _shifted(orc_f, q)[fluid]
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max()
+    assert err <= rel * scale, f"max err {err:.3e} vs scale {scale:.3e}"
+    # solids carry nothing
+    assert np.all(gpu_f[~fluid] == 0.0)
+
+
+def _masks_2d():
+    rng = np.random.default_rng(5)
+    out = {}
+    out["4x4"] = np.zeros((4, 4), np.uint8)
+    m = np.zeros((6, 8), np.uint8)
+    m[2, 3] = m[0, 5] = m[5, 1] = 1
+    out["8x6_corners"] = m
+    ch = np.zeros((8, 16), np.uint8)
+    ch[0] = ch[-1] = 1
+    out["channel16x8"] = ch
+    r = (rng.random((13, 70)) < 0.3).astype(np.uint8)  # two full segments + ragged tail
+    r[:, 0] = 0
+    out["ragged70x13"] = r
+    r2 = (rng.random((9, 96)) < 0.25).astype(np.uint8)  # exact multiple of 32
+    r2[3, 0] = 1  # a solid inlet node
+    r2[4, 95] = 1  # a solid outlet node
+    out["full96x9"] = r2
+    out["row1"] = np.zeros((1, 40), np.uint8)  # ny = 1: both mirror planes on one row
+    return out
+
+
+# --------------------------------------------------------------------------
+# QSGS: bit-exact with the oracle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,seed,phi", [
+    ((50, 100), 1, 0.74), ((13, 70), 7, 0.6), ((200, 400), 1, 0.7394), ((16, 24, 40), 3, 0.7),
+    ((8, 16), 5, 1.0), ((8, 16), 5, 0.0),
+])
+def test_qsgs_bit_exact(shape, seed, phi):
+    g, it_g = lbm.lbm_qsgs(seed, shape, 0.02, phi)
+    o, it_o = O.qsgs(shape, seed, 0.02, phi)
+    assert it_g == it_o
+    assert np.array_equal(g, o)
+
+
+def test_qsgs_all_cores_tie_break():
+    g, _ = lbm.lbm_qsgs(5, (8, 16), 1.0, 0.5)
+    o, _ = O.qsgs((8, 16), 5, 1.0, 0.5)
+    assert np.array_equal(g, o)
+
+
+# --------------------------------------------------------------------------
+# Steps from the initial state and from random states
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(_masks_2d().keys()))
+@pytest.mark.parametrize("eq", [0, 1])
+def test_d2q9_steps_from_init(name, eq):
+    mask = _masks_2d()[name]
+    tau, drho = 0.8, 1e-3
+    opts = lbm.make_options(equilibrium=eq)
+    with lbm.lbm_create_domain(mask, tau, drho, opts) as s:
+        f0 = lbm.lbm_get_populations(s, 0)
+        _assert_close(f0, O.init(mask, 1 + drho, 1.0), 9, mask)
+        ref = f0
+        done = 0
+        for n in (1, 1, 8):
+            lbm.lbm_step(s, n)
+            done += n
+            ref = O.run(mask, ref, tau, 1 + drho, 1.0, n, eq)
+            _assert_close(lbm.lbm_get_populations(s, 0), ref, 9, mask)
+
+
+@pytest.mark.parametrize("name", ["8x6_corners", "ragged70x13", "full96x9", "row1"])
+@pytest.mark.parametrize("eq", [0, 1])
+def test_d2q9_one_step_from_random_state(name, eq):
+    mask = _masks_2d()[name]
+    tau, drho = 0.67, 2e-3
+    rng = np.random.default_rng(9)
+    w = _w(9)
+    f = w * (1 + 0.05 * rng.standard_normal(mask.shape + (9,)))
+    f[mask.astype(bool)] = 0
+    with lbm.lbm_create_domain(mask, tau, drho, lbm.make_options(equilibrium=eq)) as s:
+        lbm.lbm_set_populations(s, 0, f)
+        start = lbm.lbm_get_populations(s, 0)  # FP32-rounded start
+        lbm.lbm_step(s, 1)
+        _assert_close(lbm.lbm_get_populations(s, 0), O.step(mask, start, tau, 1 + drho, 1.0, eq),
+                      9, mask)
+
+
+def _masks_3d():
+    rng = np.random.default_rng(11)
+    out = {}
+    out["4x4x4"] = np.zeros((4, 4, 4), np.uint8)
+    r = (rng.random((5, 7, 37)) < 0.3).astype(np.uint8)
+    r[..., 0] = 0
+    out["ragged37x7x5"] = r
+    out["plates"] = np.zeros((3, 8, 12), np.uint8)
+    out["plates"][:, 0] = out["plates"][:, -1] = 1
+    out["slab1"] = np.zeros((1, 6, 20), np.uint8)  # nz = 1 through the 3D entry point
+    return out
+
+
+@pytest.mark.parametrize("name", list(_masks_3d().keys()))
+@pytest.mark.parametrize("eq", [0, 1])
+def test_d3q19_steps_from_init_and_random(name, eq):
+    mask = _masks_3d()[name]
+    tau, drho = 0.9, 1e-3
+    with lbm.lbm_create_domain_3d(mask, tau, drho, lbm.make_options(equilibrium=eq)) as s:
+        f0 = lbm.lbm_get_populations(s, 0)
+        _assert_close(f0, O.init(mask, 1 + drho, 1.0), 19, mask)
+        lbm.lbm_step(s, 10)
+        _assert_close(lbm.lbm_get_populations(s, 0), O.run(mask, f0, tau, 1 + drho, 1.0, 10, eq),
+                      19, mask)
+        rng = np.random.default_rng(2)
+        f = _w(19) * (1 + 0.05 * rng.standard_normal(mask.shape + (19,)))
+        f[mask.astype(bool)] = 0
+        lbm.lbm_set_populations(s, 0, f)
+        start = lbm.lbm_get_populations(s, 0)
+        lbm.lbm_step(s, 1)
+        _assert_close(lbm.lbm_get_populations(s, 0), O.step(mask, start, tau, 1 + drho, 1.0, eq),
+                      19, mask)
+
+
+def test_rest_state_is_exactly_zero_on_device():
+    mask, _ = O.qsgs((30, 70), 4, 0.02, 0.7)
+    with lbm.lbm_create_domain(mask, 0.7, 0.0) as s:
+        lbm.lbm_step(s, 50)
+        f = lbm.lbm_get_populations(s, 0)
+        fluid = ~mask.astype(bool)
+        assert np.array_equal(f[fluid], np.broadcast_to(_w(9), f[fluid].shape))
+
+
+def test_batch_of_uneven_domains_matches_separate_oracle_runs():
+    masks = [O.qsgs((20, 50), 1, 0.02, 0.7)[0], O.qsgs((7, 33), 2, 0.02, 0.75)[0],
+             O.qsgs((31, 64), 3, 0.02, 0.65)[0]]
+    taus = [0.6, 1.1, 0.8]
+    drhos = [1e-3, 5e-4, 2e-4]
+    with lbm.lbm_batch_create(masks, taus, drhos) as s:
+        assert s.n_domains == 3
+        lbm.lbm_step(s, 7)
+        for d, m in enumerate(masks):
+            ref = O.run(m, O.init(m, 1 + drhos[d], 1.0), taus[d], 1 + drhos[d], 1.0, 7)
+            _assert_close(lbm.lbm_get_populations(s, d), ref, 9, m)
+            assert lbm.lbm_domain_fluid_nodes(s, d) == int((m == 0).sum())
+
+
+def test_observables_match_oracle_moments():
+    mask, _ = O.qsgs((24, 60), 6, 0.02, 0.72)
+    tau, drho = 0.75, 1e-3
+    with lbm.lbm_create_domain(mask, tau, drho) as s:
+        lbm.lbm_step(s, 30)
+        f_prev = lbm.lbm_get_populations(s, 0)
+        obs0 = lbm.lbm_step_observe(s, 0)  # sets u_prev to the current u
+        obs = lbm.lbm_step_observe(s, 20)[0]
+        f = lbm.lbm_get_populations(s, 0)
+    rho, ux, uy = O.fields(mask, f)
+    rp, uxp, uyp = O.fields(mask, f_prev)
+    fluid = ~mask.astype(bool)
+    jx = (rho * ux)[fluid].sum()
+    du2 = ((ux - uxp) ** 2 + (uy - uyp) ** 2)[fluid].sum()
+    u2 = (ux ** 2 + uy ** 2)[fluid].sum()
+    assert obs[0] == pytest.approx(jx, rel=1e-5)
+    assert obs[1] == pytest.approx(du2, rel=1e-3)
+    assert obs[2] == pytest.approx(u2, rel=1e-5)
+    assert obs[3] == pytest.approx(np.sqrt(ux ** 2 + uy ** 2)[fluid].max(), rel=1e-5)
+    assert obs[4] == 0
+    assert obs[5] == pytest.approx((rho - 1.0)[fluid].sum(), rel=1e-5)
+    assert obs0.shape == (1, lbm.NUM_OBS)
+
+
+# --------------------------------------------------------------------------
+# Converged permeability and fields (1e-4 / 1e-3)
+# --------------------------------------------------------------------------
+
+def _converged_oracle(mask, tau, drho, eq=0, tol=1e-10, start=None):
+    f = O.init(mask, 1 + drho, 1.0) if start is None else start
+    g, rc, steps, res = O.run_to_steady(mask, f, tau, 1 + drho, 1.0, tol, 2_000_000, eq=eq)
+    assert rc == 0, (rc, steps, res)
+    return g
+
+
+def test_small_2d_workload_permeability_and_fields():
+    wl = workloads.small_2d()
+    d = wl.domains[0]
+    mask, _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity)
+    with lbm.lbm_create_domain(mask, d.tau, d.drho) as s:
+        rc, st, steps, res = lbm.lbm_run_to_steady(s, wl.tol, wl.max_steps)
+        assert st[0] in (lbm.LBM_OK, lbm.LBM_STALLED)
+        k, kn = lbm.lbm_permeability(s)
+        rho, ux, uy = lbm.lbm_get_fields(s, 0)
+    g = _converged_oracle(mask, d.tau, d.drho)
+    k_o = O.permeability(mask, g, d.tau, 1 + d.drho, 1.0)
+    assert k[0] == pytest.approx(k_o, rel=1e-4)
+    assert kn[0] == pytest.approx(O.knudsen(d.tau, d.nx), rel=1e-14)
+    r_o, ux_o, uy_o = O.fields(mask, g)
+    num = np.sqrt(((ux - ux_o) ** 2 + (uy - uy_o) ** 2).sum())
+    den = np.sqrt((ux_o ** 2 + uy_o ** 2).sum())
+    assert num / den < 1e-3
+
+
+def test_channel_permeability_matches_exact_solution_on_device():
+    h, tau = 16, 0.8
+    mask = np.zeros((h + 2, 6 * h), np.uint8)
+    mask[0] = mask[-1] = 1
+    with lbm.lbm_create_domain(mask, tau, 1e-3, lbm.make_options(equilibrium=1)) as s:
+        lbm.lbm_run_to_steady(s, 1e-9, 200000)
+        k, _ = lbm.lbm_permeability(s)
+        f = lbm.lbm_get_populations(s, 0)
+    g = _converged_oracle(mask, tau, 1e-3, eq=1, tol=1e-12)
+    assert k[0] == pytest.approx(O.permeability(mask, g, tau, 1.001, 1.0), rel=1e-4)
+
+
+def test_checkpoint_round_trip_is_bitwise(tmp_path):
+    mask, _ = O.qsgs((20, 45), 8, 0.02, 0.72)
+    p = str(tmp_path / "c.ckpt")
+    with lbm.lbm_create_domain(mask, 0.9, 1e-3) as a:
+        lbm.lbm_step(a, 37)
+        lbm.lbm_save(a, p)
+        lbm.lbm_step(a, 25)
+        fa = lbm.lbm_get_populations(a, 0)
+    with lbm.lbm_load(p, masks=[mask]) as b:
+        assert lbm.lbm_get_step(b) == 37
+        lbm.lbm_step(b, 25)
+        fb = lbm.lbm_get_populations(b, 0)
+    assert np.array_equal(fa, fb)
+
+
+def test_divergence_is_reported():
+    mask = np.zeros((8, 20), np.uint8)
+    with lbm.lbm_create_domain(mask, 0.8, 1e-3) as s:
+        f = lbm.lbm_get_populations(s, 0)
+        f[3, 5, 2] = np.nan
+        lbm.lbm_set_populations(s, 0, f)
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_run_to_steady(s, 1e-9, 1000)
+        assert e.value.status == lbm.LBM_DIVERGED
