@@ -30,37 +30,42 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags():
+def _flags(defines=()):
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-I", INCLUDE, "-I", CSRC]
+                   "-I", INCLUDE, "-I", CSRC] + [f"-D{d}" for d in defines]
 
 
-def _stamp(srcs):
+def _stamp(srcs, defines=()):
     h = hashlib.sha256()
     for f in sorted(srcs + glob.glob(os.path.join(CSRC, "*.h*")) + [os.path.join(INCLUDE, "lbm.h")]):
         with open(f, "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
-    h.update(" ".join(_flags()).encode())
+    h.update(" ".join(_flags(defines)).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, defines=(), out: str = None) -> str:
+    """Compile and link the library; `defines` are extra -D tuning macros and
+    `out` an alternative output path (both for tuning sweeps)."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    os.makedirs(LIBDIR, exist_ok=True)
-    stamp_file = os.path.join(LIBDIR, "stamp.txt")
-    stamp = _stamp(srcs)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+    lib = out or LIB
+    libdir = os.path.dirname(lib)
+    os.makedirs(libdir, exist_ok=True)
+    stamp_file = lib + ".stamp"
+    stamp = _stamp(srcs, defines)
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         with open(stamp_file) as fh:
             if fh.read().strip() == stamp:
-                return LIB
+                return lib
     cc = nvcc()
-    objs = [os.path.join(LIBDIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    tag = hashlib.sha256(lib.encode()).hexdigest()[:8]
+    objs = [os.path.join(libdir, os.path.basename(s)[:-3] + f".{tag}.o") for s in srcs]
 
     def compile_one(src_obj):
         src, obj = src_obj
-        cmd = [cc] + _flags() + ["-c", src, "-o", obj]
+        cmd = [cc] + _flags(defines) + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -73,15 +78,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for l in logs:
             sys.stderr.write(l)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

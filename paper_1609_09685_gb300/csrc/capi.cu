@@ -72,6 +72,9 @@ struct lbm_solver {
     uint32_t* d_seg_off = nullptr;
     uint32_t* d_seg_cnt = nullptr;
     uint32_t* d_scan = nullptr;
+    uint4* d_win = nullptr;
+    uint4* d_items = nullptr;
+    uint32_t nitems = 0;
     uint8_t* d_mask = nullptr;
     uint32_t nseg_total = 0;
     uint64_t nfluid = 0, pstride = 0;
@@ -94,6 +97,15 @@ struct lbm_solver {
         G.nseg_total = nseg_total;
         G.pstride = pstride;
         return G;
+    }
+    HotArgs hot() const {
+        HotArgs A;
+        A.dom = d_dom;
+        A.win = d_win;
+        A.items = d_items;
+        A.nitems = nitems;
+        A.pstride = (uint32_t)pstride;
+        return A;
     }
 };
 
@@ -128,6 +140,8 @@ void free_solver(lbm_handle h) {
     cudaFree(h->d_seg_off);
     cudaFree(h->d_seg_cnt);
     cudaFree(h->d_scan);
+    cudaFree(h->d_win);
+    cudaFree(h->d_items);
     cudaFree(h->d_mask);
     cudaFree(h->d_g[0]);
     cudaFree(h->d_g[1]);
@@ -152,15 +166,16 @@ lbm_status upload_dom(lbm_handle h) {
 // copy of the observables to pinned host memory.  Advances h->cur.
 lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs) {
     const Geometry G = h->geom();
+    const HotArgs A = h->hot();
     for (int64_t k = 0; k < n; ++k) {
         const bool o = obs && (k == n - 1);
-        CK(h, launch_stream_collide(h->q, h->eq, o, G, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
+        CK(h, launch_stream_collide(h->q, h->eq, o, A, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
                                     h->d_partials, h->opt.block_threads, h->st));
         h->cur ^= 1;
     }
     if (obs) {
         if (n == 0) CK(h, launch_observe(h->q, G, h->d_g[h->cur], h->d_uprev, h->d_partials, h->st));
-        CK(h, launch_reduce_obs(h->d_dom, (int)h->dom.size(), h->d_partials, h->d_obs, h->st));
+        CK(h, launch_reduce_obs(h->d_dom, (int)h->dom.size(), h->d_partials, h->d_obs, n > 0, h->st));
         CK(h, cudaMemcpyAsync(h->h_obs, h->d_obs, sizeof(double) * kNumObs * h->dom.size(),
                               cudaMemcpyDeviceToHost, h->st));
     }
@@ -262,6 +277,7 @@ void lbm_options_default(lbm_options* o) {
     o->block_threads = 0;
     o->use_graphs = 1;
     o->cancel_flag = nullptr;
+    o->strip_rows = 0;
 }
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
@@ -320,7 +336,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     }
     if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) ||
         (o.equilibrium != LBM_EQ_QUADRATIC && o.equilibrium != LBM_EQ_LINEAR) || o.block_threads < 0 ||
-        o.block_threads > 1024 || (o.block_threads % 32) != 0)
+        o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255)
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     int q = force_q;
     if (!q) {
@@ -333,6 +349,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         const lbm_domain_desc& D = descs[d];
         if (!D.mask) return fail(nullptr, LBM_ERR_ARG, "domain mask is null");
         if (D.nx < 3 || D.ny < 1 || D.nz < 1) return fail(nullptr, LBM_ERR_ARG, "need nx >= 3, ny >= 1, nz >= 1");
+        if (D.ny > 65535 || D.nz > 65535) return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
         if (q == 9 && D.nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 domains need nz = 1");
         if (!(D.tau > 0.5) || !std::isfinite(D.tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be > 0.5");
         if (!std::isfinite(D.drho) || std::fabs(D.drho) >= o.rho_out)
@@ -343,7 +360,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         segs += (uint64_t)((D.nx + kSegW - 1) / kSegW) * D.ny * D.nz;
         cells += N;
     }
-    if (segs >= (1ull << 32) || cells >= (1ull << 32)) return fail(nullptr, LBM_ERR_ARG, "batch too large");
+    if (segs >= (1ull << 32) || (cells + 32) * q >= (1ull << 32) || n >= (1 << 24))
+        return fail(nullptr, LBM_ERR_ARG, "batch too large (Q x nodes must stay below 2^32)");
 
     lbm_handle h = new lbm_solver();
     h->q = q;
@@ -423,9 +441,10 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     const uint32_t nscan = (sb + 1023) / 1024;
     CKC(launch_seg_setup(h->d_dom, h->d_dom_begin, n, sb, h->d_mask, h->d_seg_dom, h->d_seg_mask, h->d_seg_cnt,
                          h->d_seg_off, h->d_scan, h->d_scan + nscan + 1, h->st));
-    std::vector<uint32_t> off(sb + 1);
+    std::vector<uint32_t> off(sb + 1), smask(std::max<uint32_t>(sb, 1));
     uint32_t total = 0;
     CKC(cudaMemcpyAsync(off.data(), h->d_seg_off, sizeof(uint32_t) * sb, cudaMemcpyDeviceToHost, h->st));
+    CKC(cudaMemcpyAsync(smask.data(), h->d_seg_mask, sizeof(uint32_t) * sb, cudaMemcpyDeviceToHost, h->st));
     CKC(cudaMemcpyAsync(&total, h->d_scan + nscan + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st));
     CKC(cudaStreamSynchronize(h->st));
     off[sb] = total;
@@ -434,12 +453,44 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         h->dom[d].fluid_begin = off[begin[d]];
         h->dom[d].fluid_count = off[begin[d + 1]] - off[begin[d]];
     }
-    h->pstride = ((std::max<uint64_t>(total, 1) + 31) / 32) * 32;
+    // Strip work list: per domain and z plane, runs of up to R rows at each
+    // segment column, with the column innermost so that warps of one block (and
+    // neighbouring blocks) sweep adjacent segments of the same rows -- contiguous
+    // compact ranges in every population plane.  Strips whose segments are all
+    // solid are left out.
+    const int R = o.strip_rows > 0 ? o.strip_rows : 8;
+    std::vector<uint4> items;
+    for (int d = 0; d < n; ++d) {
+        DomainDev& G = h->hdom[d];
+        G.item_base = (uint32_t)items.size();
+        for (int z = 0; z < G.nz; ++z)
+            for (int y0 = 0; y0 < G.ny; y0 += R)
+                for (int sidx = 0; sidx < G.nseg; ++sidx) {
+                    const int nr = std::min(R, G.ny - y0);
+                    const uint32_t g0 = G.seg_base + ((uint32_t)z * G.ny + y0) * G.nseg + sidx;
+                    bool any = false;
+                    for (int k = 0; k < nr && !any; ++k) any = smask[g0 + (uint32_t)k * G.nseg] != 0u;
+                    if (!any) continue;
+                    items.push_back(make_uint4(g0, (uint32_t)d | ((uint32_t)nr << 24),
+                                               (uint32_t)y0 | ((uint32_t)z << 16), (uint32_t)sidx));
+                }
+        G.nitems = (uint32_t)items.size() - G.item_base;
+    }
+    h->nitems = (uint32_t)items.size();
+    CKC(cudaMalloc(&h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
+    CKC(cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
+    CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
+    CKC(cudaMalloc(&h->d_win, sizeof(uint4) * std::max<uint32_t>(sb, 1)));
+    CKC(launch_build_windows(h->d_dom, h->d_seg_dom, sb, h->d_seg_mask, h->d_seg_off, h->d_win, h->st));
+    CKC(cudaStreamSynchronize(h->st));
+    // one padding slot past the last fluid node: the stream-collide kernel
+    // loads unconditionally and a solid lane may address slot nfluid
+    h->pstride = ((uint64_t)total + 1 + 31) / 32 * 32;
     const int D = (q == 9) ? 2 : 3;
     CKC(cudaMalloc(&h->d_g[0], sizeof(float) * q * h->pstride));
     CKC(cudaMalloc(&h->d_g[1], sizeof(float) * q * h->pstride));
     CKC(cudaMalloc(&h->d_uprev, sizeof(float) * D * h->pstride));
-    CKC(cudaMalloc(&h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(sb, 1)));
+    CKC(cudaMalloc(&h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
     CKC(cudaMalloc(&h->d_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));

@@ -70,6 +70,33 @@ struct DomainDev {
     float rho0;          // rho_0 = rho_out
     int32_t active;      // 0 once retired by the steady-state control
     uint64_t mask_base;  // byte offset of the domain's dense mask
+    uint32_t item_base;  // first strip work item of the domain
+    uint32_t nitems;     // strip work items of the domain
+};
+
+// Neighbour window of one segment, read by the stream-collide kernel:
+//   x = lo | hi << 32 holds 34 fluid bits, bit k <-> node x = 32 s - 1 + k
+//   (the left neighbour's last node, the segment's 32 nodes, the right
+//   neighbour's first node); z = compact index of node 32 s - 1 if that node is
+//   fluid, else of the segment's first fluid node (offset - left bit);
+//   w = the segment's own mask.
+using SegWindow = uint4;
+
+// Strip work item: up to 255 consecutive rows y0 .. y0 + nrows - 1 (one z
+// plane) at segment column s of one domain.
+//   x = global segment of (s, y0, z); y = domain | nrows << 24;
+//   z = y0 | z << 16;                  w = s.
+using StripItem = uint4;
+
+// Arguments of the hot stream-collide kernel.
+struct HotArgs {
+    const DomainDev* dom;
+    const SegWindow* win;
+    const StripItem* items;
+    uint32_t nitems;
+    uint32_t pstride;        // elements between direction planes (Q * pstride < 2^32)
+    const float* src[19];    // direction planes of the state being read
+    float* dst[19];          // direction planes of the state being written
 };
 
 // Arguments shared by every segment kernel.

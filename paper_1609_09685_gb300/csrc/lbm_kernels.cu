@@ -21,6 +21,8 @@
 //   equilibrium with relaxation 1/tau.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
@@ -97,106 +99,279 @@ __device__ __forceinline__ void zou_he(float (&f)[L::Q], float drho_b) {
 // ---------------------------------------------------------------------------
 // Fused stream + boundaries + BGK collide; OBS adds the per-interval FP64
 // reductions (flux, residual terms, max |u|, non-finite count, mass).
+//
+// A warp walks one strip (consecutive rows of one segment column).  For each
+// row it reads the neighbour window of every row it pulls from (the row above,
+// its own, the row below; in 3D also the planes in front and behind).  Lane l
+// shifts the 34-bit window by l: bits 0, 1, 2 are the fluid flags of the
+// sources at x - 1, x, x + 1, i.e. for c_x = +1, 0, -1, and the compact index
+// of the c_x = +1 source is the window base plus a popcount below lane l.
 // ---------------------------------------------------------------------------
+namespace {
+
+struct Win {
+    uint32_t tri;  // fluid flags of nodes x - 1, x, x + 1 in the window's row
+    uint32_t i0;   // compact index of node x - 1 (valid when that node is fluid)
+};
+
+__device__ __forceinline__ Win make_win(const uint4 r, int lane, uint32_t lmask) {
+    const uint64_t W = ((uint64_t)r.y << 32) | r.x;
+    Win w;
+    w.tri = (uint32_t)(W >> lane) & 7u;
+    w.i0 = r.z + __popc(r.x & lmask);
+    return w;
+}
+template <int CX>
+__device__ __forceinline__ uint32_t win_idx(const Win& w) {
+    return CX == 1 ? w.i0 : (CX == 0 ? w.i0 + (w.tri & 1u) : w.i0 + (w.tri & 1u) + ((w.tri >> 1) & 1u));
+}
+template <int CX>
+__device__ __forceinline__ bool win_fluid(const Win& w) {
+    return (w.tri >> (1 - CX)) & 1u;
+}
+template <int I, class L>
+struct Dir {
+    static constexpr int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
+    static constexpr int o = opp<L>(I);
+    static constexpr int fy = flip<L>(I, true, false), fz = flip<L>(I, false, true),
+                         fyz = flip<L>(I, true, true);
+    static constexpr int row = (1 - cy) + (L::NROW == 9 ? 3 * (1 - cz) : 0);
+};
+
+// Source of direction I for the node of window set w (pull streaming): the
+// fluid source's compact slot in the (possibly mirrored) direction plane, or
+// the node's own opposite slot when the source is solid (bounce-back).
+template <class L, int I>
+__device__ __forceinline__ const float* src_ptr(const HotArgs& A, const Win (&w)[L::NROW], uint32_t kd, bool my,
+                                                bool mz) {
+    using d = Dir<I, L>;
+    const Win& wn = w[d::row];
+    const bool sf = win_fluid<d::cx>(wn);
+    const float* plane = A.src[I];
+    if (d::cy != 0 && d::cz != 0) plane = my ? (mz ? A.src[d::fyz] : A.src[d::fy]) : (mz ? A.src[d::fz] : A.src[I]);
+    else if (d::cy != 0) plane = my ? A.src[d::fy] : A.src[I];
+    else if (d::cz != 0) plane = mz ? A.src[d::fz] : A.src[I];
+    return sf ? plane + win_idx<d::cx>(wn) : A.src[d::o] + kd;
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const float* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue the Q source loads of one row into shared-memory stage `sbase`
+// (slot (i, lane) at sbase + 4 (32 i + lane)).  For a solid lane kd is the
+// slot of the next fluid node (at most the padding slot nfluid < pstride), so
+// every address is in bounds; the value is discarded.
+template <class L, int... Is>
+__device__ __forceinline__ void issue_row(const HotArgs& A, const Win (&w)[L::NROW], uint32_t kd, bool ylo,
+                                          bool yhi, bool zlo, bool zhi, uint32_t sbase,
+                                          std::integer_sequence<int, Is...>) {
+    // a direction with c_y = +1 pulls from row y - 1, mirrored when y = 0, etc.
+    (cp_async4(sbase + 4u * (32u * Is),
+               src_ptr<L, Is>(A, w, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, Dir<Is, L>::cz > 0 ? zlo : zhi)),
+     ...);
+}
+
+}  // namespace
+
+// Minimum resident 256-thread blocks per SM for the stream-collide kernel
+// (caps registers per thread: 65536 / (256 * MINB)).
+#ifndef LBM_SC_MINB_2D
+#define LBM_SC_MINB_2D 4
+#endif
+#ifndef LBM_SC_MINB_3D
+#define LBM_SC_MINB_3D 2
+#endif
+template <class L>
+struct MinBlocks {
+    static constexpr int value = (L::Q == 9) ? LBM_SC_MINB_2D : LBM_SC_MINB_3D;
+};
+
+#ifndef LBM_SC_STAGES
+#define LBM_SC_STAGES 3  // rows in flight per warp in the cp.async pipeline
+#endif
+constexpr int kStages = LBM_SC_STAGES;
+
+template <class L>
+constexpr size_t sc_smem_bytes(int threads) {
+    return (size_t)(threads / 32) * kStages * L::Q * 32 * sizeof(float);
+}
+
+// A warp walks its strip row by row.  Rows k+1 .. k+S-1 are already in
+// flight as cp.async copies into the warp's shared-memory stages while row k
+// is relaxed and stored, so loads overlap compute without holding registers.
 template <class L, int EQ, bool OBS>
-__global__ void __launch_bounds__(256)
-    k_stream_collide(Geometry G, const float* __restrict__ src, float* __restrict__ dst,
-                     float* __restrict__ uprev, double* __restrict__ partials) {
+__global__ void __launch_bounds__(256, MinBlocks<L>::value)
+    k_stream_collide(const __grid_constant__ HotArgs A, float* __restrict__ uprev, double* __restrict__ partials) {
     constexpr int Q = L::Q;
+    constexpr int NZ = (L::NROW == 9) ? 3 : 1;
+    constexpr int S = kStages;
+    extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
-    const uint32_t gseg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (gseg >= G.nseg_total) return;
-    const uint32_t d = __ldg(G.seg_dom + gseg);
-    const DomainDev D = G.dom[d];
-    const uint32_t mc = __ldg(G.seg_mask + gseg);
-    if (!D.active || mc == 0u) {
-        if (OBS && lane < kNumObs) partials[(size_t)gseg * kNumObs + lane] = 0.0;
+    const int wid = threadIdx.x >> 5;
+    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (item >= A.nitems) return;
+    const uint4 it = __ldg(A.items + item);
+    const uint32_t dom = it.y & 0xffffffu;
+    const int nrows = (int)(it.y >> 24);
+    const DomainDev D = A.dom[dom];
+    if (!D.active) {
+        if (OBS && lane < kNumObs) partials[(size_t)item * kNumObs + lane] = 0.0;
         return;
     }
-    const SegLoc P = locate(D, gseg, lane);
+    const int y0 = (int)(it.z & 0xffffu), z = (int)(it.z >> 16);
+    const int x = (int)it.w * kSegW + lane;
+    const uint32_t lmask = (1u << lane) - 1u;
+    const uint32_t PS = A.pstride;
+    const int ny = D.ny;
+    const bool zlo = (z == 0), zhi = (z == D.nz - 1);
+    const bool xin = (x == 0), xout = (x == D.nx - 1);
+    const bool edge = (it.w == 0) || ((int)it.w == D.nseg - 1);
+    // omega-scaled weights by |c|^2 class (0 rest, 1 axis, 2 diagonal) and 3x them
+    const float om = D.omega, omc = 1.0f - D.omega;
+    const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
+    const float ow3[3] = {3.0f * ow[0], 3.0f * ow[1], 3.0f * ow[2]};
+    float* const* dst = A.dst;
+    float* wbuf = smem + (size_t)wid * S * Q * 32;
+    const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(wbuf) + 4u * lane;
+    // Window records of planes z-1, z, z+1 and rows clamped onto the domain
+    // (the clamped row or plane is the mirror image at a specular face).
+    const SegWindow* wcol = A.win + D.seg_base + it.w;
+    const uint32_t rs = (uint32_t)D.nseg;
+    uint32_t pbase[NZ];
+#pragma unroll
+    for (int zi = 0; zi < NZ; ++zi) {
+        int zz = z + zi - (NZ == 3 ? 1 : 0);
+        zz = zz < 0 ? 0 : (zz >= D.nz ? D.nz - 1 : zz);
+        pbase[zi] = (uint32_t)zz * (uint32_t)ny;
+    }
+    auto rowc = [&](int yy) { return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy); };
+    // windows of rows r-1, r, r+1 for the next row r to issue, and the raw
+    // record of row r+2 loaded one issue ahead
+    Win wm[NZ], wc[NZ], wp[NZ];
+    uint4 rn[NZ];
+#pragma unroll
+    for (int zi = 0; zi < NZ; ++zi) {
+        wm[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 - 1)) * rs), lane, lmask);
+        wc[zi] = make_win(__ldg(wcol + (pbase[zi] + y0) * rs), lane, lmask);
+        wp[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 + 1)) * rs), lane, lmask);
+        rn[zi] = __ldg(wcol + (pbase[zi] + rowc(y0 + 2)) * rs);
+    }
+    int next = 0;  // next row (relative to y0) to issue
+    bool flq[S];
+    uint32_t kdq[S];
+    // issue row `next` into stage st, then slide the windows one row down
+    auto issue = [&](int st) {
+        if (next < nrows) {
+            const int y = y0 + next;
+            Win w[L::NROW];
+#pragma unroll
+            for (int r = 0; r < L::NROW; ++r) {
+                const int zi = (NZ == 3) ? r / 3 : 0, dy = r % 3;
+                w[r] = dy == 0 ? wm[zi] : (dy == 1 ? wc[zi] : wp[zi]);
+            }
+            constexpr int C = (L::NROW == 9) ? 4 : 1;
+            flq[st] = win_fluid<0>(w[C]);
+            kdq[st] = win_idx<0>(w[C]);
+            issue_row<L>(A, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sb0 + 4u * (uint32_t)(st * Q * 32),
+                         std::make_integer_sequence<int, Q>{});
+            if (next + 1 < nrows) {
+#pragma unroll
+                for (int zi = 0; zi < NZ; ++zi) {
+                    wm[zi] = wc[zi];
+                    wc[zi] = wp[zi];
+                    wp[zi] = make_win(rn[zi], lane, lmask);
+                    rn[zi] = __ldg(wcol + (pbase[zi] + rowc(y + 3)) * rs);
+                }
+            }
+        } else {
+            flq[st] = false;
+            kdq[st] = 0u;
+        }
+        ++next;
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int st = 0; st < S - 1; ++st) issue(st);
 
-    // Neighbourhood metadata: lane e < 3 NROW holds segment s + (e % 3) - 1 of
-    // row (y + dy, z + dz) with e / 3 = (dy + 1) + 3 (dz + 1); a row outside the
-    // domain is replaced by the node's own row (the mirror image).
-    uint32_t nbm = 0u, nbo = 0u;
-    if (lane < 3 * L::NROW) {
-        const int r = lane / 3, cs = lane - 3 * r;
-        int yy = P.y + (r % 3) - 1;
-        int zz = P.z + (L::NROW == 9 ? r / 3 - 1 : 0);
-        if (yy < 0 || yy >= D.ny) yy = P.y;
-        if (zz < 0 || zz >= D.nz) zz = P.z;
-        const int ss = P.s + cs - 1;
-        if (ss >= 0 && ss < D.nseg) {
-            const uint32_t g2 = D.seg_base + ((uint32_t)zz * D.ny + yy) * D.nseg + ss;
-            nbm = __ldg(G.seg_mask + g2);
-            nbo = __ldg(G.seg_off + g2);
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0;
+    for (int k = 0; k < nrows; k += S) {
+#pragma unroll
+        for (int st = 0; st < S; ++st) {
+            if (k + st >= nrows) break;
+            issue((st + S - 1) % S);
+            cp_async_wait<S - 1>();
+            const float* sf = wbuf + st * Q * 32 + lane;
+            float f[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = sf[i * 32];
+            const bool fl = flq[st];
+            const uint32_t kk = kdq[st];
+            if (edge) {  // warp-uniform: only the first and last segment columns hold x faces
+                float g[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = f[i];
+                zou_he<L, +1>(g, D.drho_in);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = xin ? g[i] : f[i];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = f[i];
+                zou_he<L, -1>(g, 0.f);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = xout ? g[i] : f[i];
+            }
+            float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                dr += f[i];
+                jx += (float)L::c(i, 0) * f[i];
+                jy += (float)L::c(i, 1) * f[i];
+                jz += (float)L::c(i, 2) * f[i];
+            }
+            const float irho = __fdividef(1.0f, D.rho0 + dr);
+            if (fl) {
+                // BGK by opposite pairs: f* = (1 - omega) f + omega w (a0 + 4.5 (c.j)^2/rho +- 3 c.j),
+                // a0 = drho - 1.5 |j|^2 / rho (quadratic) or drho (linear).
+                const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jx * jx + jy * jy + jz * jz, dr) : dr;
+                const float k45 = 4.5f * irho;
+                dst[0][kk] = fmaf(omc, f[0], ow[0] * a0);
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    if (opp<L>(i) < i) continue;
+                    const int o = opp<L>(i);
+                    const int cls = (L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
+                    const float cj = (float)L::c(i, 0) * jx + (float)L::c(i, 1) * jy + (float)L::c(i, 2) * jz;
+                    const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
+                    const float anti = ow3[cls] * cj;
+                    dst[i][kk] = fmaf(omc, f[i], sym + anti);
+                    dst[o][kk] = fmaf(omc, f[o], sym - anti);
+                }
+                if (OBS) {
+                    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+                    const float px = uprev[kk], py = uprev[PS + kk];
+                    const float pz = (L::D == 3) ? uprev[2u * PS + kk] : 0.f;
+                    const float ex = ux - px, ey = uy - py, ez = uz - pz;
+                    const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+                    v0 += (double)jx;
+                    v1 += (double)ex * ex + (double)ey * ey + (double)ez * ez;
+                    v2 += u2;
+                    v3 = fmax(v3, sqrt(u2));
+                    v4 += (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? 0.0 : 1.0;
+                    v5 += (double)dr;
+                    uprev[kk] = ux;
+                    uprev[PS + kk] = uy;
+                    if (L::D == 3) uprev[2u * PS + kk] = uz;
+                }
+            }
         }
     }
-    const bool fluid = (mc >> lane) & 1u;
-    const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
-    const size_t PS = G.pstride;
-
-    float f[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-        const int sx = P.x - cx;
-        const bool fy = (cy != 0) && (P.y - cy < 0 || P.y - cy >= D.ny);
-        const bool fz = (cz != 0) && (P.z - cz < 0 || P.z - cz >= D.nz);
-        const int r = (1 - cy) + (L::NROW == 9 ? 3 * (1 - cz) : 0);
-        const int e = 3 * r + ((sx >> 5) - P.s + 1);
-        const uint32_t m = __shfl_sync(kFull, nbm, e);
-        const uint32_t o = __shfl_sync(kFull, nbo, e);
-        const int j = fy ? (fz ? flip<L>(i, true, true) : flip<L>(i, true, false))
-                         : (fz ? flip<L>(i, false, true) : i);
-        const uint32_t bit = (uint32_t)sx & 31u;
-        const bool sf = (m >> bit) & 1u;
-        const size_t a = sf ? (size_t)j * PS + o + __popc(m & ((1u << bit) - 1u))
-                            : (size_t)opp<L>(i) * PS + kd;
-        f[i] = fluid ? __ldg(src + a) : 0.f;
-    }
-    if (P.x == 0) zou_he<L, +1>(f, D.drho_in);
-    if (P.x == D.nx - 1) zou_he<L, -1>(f, 0.f);
-
-    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        dr += f[i];
-        jx += (float)L::c(i, 0) * f[i];
-        jy += (float)L::c(i, 1) * f[i];
-        jz += (float)L::c(i, 2) * f[i];
-    }
-    const float rho = D.rho0 + dr;
-    const float irho = 1.0f / rho;
-    const float jj = jx * jx + jy * jy + jz * jz;
-    if (fluid) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float cj = (float)L::c(i, 0) * jx + (float)L::c(i, 1) * jy + (float)L::c(i, 2) * jz;
-            const float w = (float)L::wd(i);
-            float geq = dr + 3.0f * cj;
-            if (EQ == 0) geq += (4.5f * cj * cj - 1.5f * jj) * irho;
-            geq *= w;
-            dst[(size_t)i * PS + kd] = f[i] + D.omega * (geq - f[i]);
-        }
-    }
+    cp_async_wait<0>();
     if (OBS) {
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0;
-        if (fluid) {
-            const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
-            const float px = uprev[kd], py = uprev[PS + kd];
-            const float pz = (L::D == 3) ? uprev[2 * PS + kd] : 0.f;
-            const float ex = ux - px, ey = uy - py, ez = uz - pz;
-            v0 = (double)jx;
-            v1 = (double)ex * ex + (double)ey * ey + (double)ez * ez;
-            v2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-            v3 = sqrt(v2);
-            v4 = isfinite(ux) && isfinite(uy) && isfinite(uz) ? 0.0 : 1.0;
-            v5 = (double)dr;
-            uprev[kd] = ux;
-            uprev[PS + kd] = uy;
-            if (L::D == 3) uprev[2 * PS + kd] = uz;
-        }
         v0 = warp_sum(v0);
         v1 = warp_sum(v1);
         v2 = warp_sum(v2);
@@ -204,7 +379,7 @@ __global__ void __launch_bounds__(256)
         v4 = warp_sum(v4);
         v5 = warp_sum(v5);
         if (lane == 0) {
-            double* p = partials + (size_t)gseg * kNumObs;
+            double* p = partials + (size_t)item * kNumObs;
             p[0] = v0;
             p[1] = v1;
             p[2] = v2;
@@ -215,6 +390,25 @@ __global__ void __launch_bounds__(256)
             p[7] = 0.0;
         }
     }
+}
+
+// Neighbour windows of every segment (see SegWindow).
+__global__ void k_build_windows(const DomainDev* __restrict__ dom, const uint32_t* __restrict__ seg_dom,
+                                uint32_t nseg_total, const uint32_t* __restrict__ seg_mask,
+                                const uint32_t* __restrict__ seg_off, uint4* __restrict__ win) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg_total) return;
+    const DomainDev D = dom[seg_dom[g]];
+    const uint32_t s = (g - D.seg_base) % (uint32_t)D.nseg;
+    const uint32_t own = seg_mask[g];
+    const uint32_t left = s > 0 ? seg_mask[g - 1] >> 31 : 0u;
+    const uint32_t right = (s + 1 < (uint32_t)D.nseg) ? seg_mask[g + 1] & 1u : 0u;
+    uint4 r;
+    r.x = left | (own << 1);
+    r.y = (own >> 31) | (right << 1);
+    r.z = seg_off[g] - left;
+    r.w = own;
+    win[g] = r;
 }
 
 // Observation of the current state without stepping: the same reductions as
@@ -280,10 +474,11 @@ __global__ void __launch_bounds__(256)
 // Per-domain second pass over the warp partials in a fixed order (deterministic).
 __global__ void __launch_bounds__(256)
     k_reduce_obs(const DomainDev* __restrict__ dom, const double* __restrict__ partials,
-                 double* __restrict__ obs) {
+                 double* __restrict__ obs, int item_mode) {
     __shared__ double sh[kNumObs][256];
     const int d = blockIdx.x;
-    const uint32_t base = dom[d].seg_base, n = dom[d].nseg_dom;
+    const uint32_t base = item_mode ? dom[d].item_base : dom[d].seg_base;
+    const uint32_t n = item_mode ? dom[d].nitems : dom[d].nseg_dom;
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const double* p = partials + (size_t)(base + i) * kNumObs;
@@ -549,27 +744,51 @@ inline unsigned seg_blocks(uint32_t nseg, int threads) {
 }
 }  // namespace
 
-template <class L>
-static cudaError_t sc_dispatch(int eq, bool obs, const Geometry& G, const float* src, float* dst,
-                               float* uprev, double* partials, int threads, cudaStream_t st) {
-    const unsigned nb = seg_blocks(G.nseg_total, threads);
-    if (nb == 0) return cudaSuccess;
-    if (eq == 0) {
-        if (obs) k_stream_collide<L, 0, true><<<nb, threads, 0, st>>>(G, src, dst, uprev, partials);
-        else k_stream_collide<L, 0, false><<<nb, threads, 0, st>>>(G, src, dst, uprev, partials);
-    } else {
-        if (obs) k_stream_collide<L, 1, true><<<nb, threads, 0, st>>>(G, src, dst, uprev, partials);
-        else k_stream_collide<L, 1, false><<<nb, threads, 0, st>>>(G, src, dst, uprev, partials);
+template <class L, int EQ, bool OBS>
+static cudaError_t sc_launch(unsigned nb, int threads, const HotArgs& A, float* uprev, double* partials,
+                             cudaStream_t st) {
+    const size_t sm = sc_smem_bytes<L>(threads);
+    static bool attr_set = false;  // per template instance; the attribute is per device function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_collide<L, EQ, OBS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem_bytes<L>(256));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
     }
+    k_stream_collide<L, EQ, OBS><<<nb, threads, sm, st>>>(A, uprev, partials);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_collide(int q, int eq, bool obs, const Geometry& G, const float* src,
-                                  float* dst, float* uprev, double* partials, int threads,
-                                  cudaStream_t st) {
+template <class L>
+static cudaError_t sc_dispatch(int eq, bool obs, const HotArgs& A, float* uprev, double* partials, int threads,
+                               cudaStream_t st) {
+    const unsigned nb = seg_blocks(A.nitems, threads);
+    if (nb == 0) return cudaSuccess;
+    if (eq == 0) {
+        if (obs) return sc_launch<L, 0, true>(nb, threads, A, uprev, partials, st);
+        return sc_launch<L, 0, false>(nb, threads, A, uprev, partials, st);
+    }
+    if (obs) return sc_launch<L, 1, true>(nb, threads, A, uprev, partials, st);
+    return sc_launch<L, 1, false>(nb, threads, A, uprev, partials, st);
+}
+
+cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const float* src, float* dst,
+                                  float* uprev, double* partials, int threads, cudaStream_t st) {
     if (threads <= 0) threads = 256;
-    if (q == 9) return sc_dispatch<D2Q9>(eq, obs, G, src, dst, uprev, partials, threads, st);
-    return sc_dispatch<D3Q19>(eq, obs, G, src, dst, uprev, partials, threads, st);
+    for (int i = 0; i < 19; ++i) {
+        A.src[i] = i < q ? src + (size_t)i * A.pstride : nullptr;
+        A.dst[i] = i < q ? dst + (size_t)i * A.pstride : nullptr;
+    }
+    if (q == 9) return sc_dispatch<D2Q9>(eq, obs, A, uprev, partials, threads, st);
+    return sc_dispatch<D3Q19>(eq, obs, A, uprev, partials, threads, st);
+}
+
+cudaError_t launch_build_windows(const DomainDev* dom, const uint32_t* seg_dom, uint32_t nseg_total,
+                                 const uint32_t* seg_mask, const uint32_t* seg_off, uint4* win,
+                                 cudaStream_t st) {
+    if (nseg_total == 0) return cudaSuccess;
+    k_build_windows<<<(nseg_total + 255) / 256, 256, 0, st>>>(dom, seg_dom, nseg_total, seg_mask, seg_off, win);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_observe(int q, const Geometry& G, const float* g, float* uprev, double* partials,
@@ -582,9 +801,9 @@ cudaError_t launch_observe(int q, const Geometry& G, const float* g, float* upre
 }
 
 cudaError_t launch_reduce_obs(const DomainDev* dom, int ndom, const double* partials, double* obs,
-                              cudaStream_t st) {
+                              bool item_mode, cudaStream_t st) {
     if (ndom <= 0) return cudaSuccess;
-    k_reduce_obs<<<ndom, 256, 0, st>>>(dom, partials, obs);
+    k_reduce_obs<<<ndom, 256, 0, st>>>(dom, partials, obs, item_mode ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -8,13 +8,17 @@
 
 namespace lbmgb {
 
-cudaError_t launch_stream_collide(int q, int eq, bool obs, const Geometry& G, const float* src,
-                                  float* dst, float* uprev, double* partials, int threads,
-                                  cudaStream_t st);
+cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const float* src, float* dst,
+                                  float* uprev, double* partials, int threads, cudaStream_t st);
+cudaError_t launch_build_windows(const DomainDev* dom, const uint32_t* seg_dom, uint32_t nseg_total,
+                                 const uint32_t* seg_mask, const uint32_t* seg_off, uint4* win,
+                                 cudaStream_t st);
 cudaError_t launch_observe(int q, const Geometry& G, const float* g, float* uprev, double* partials,
                            cudaStream_t st);
+// item_mode: partials are per strip item (stream-collide) rather than per
+// segment (observe-only kernel).
 cudaError_t launch_reduce_obs(const DomainDev* dom, int ndom, const double* partials, double* obs,
-                              cudaStream_t st);
+                              bool item_mode, cudaStream_t st);
 cudaError_t launch_init(int q, const Geometry& G, float* g, float* uprev, cudaStream_t st);
 cudaError_t launch_export_pops(int q, const Geometry& G, uint32_t base, uint32_t nseg, double rho0,
                                const float* g, double* out, cudaStream_t st);

@@ -54,6 +54,7 @@ class lbm_options(C.Structure):
         ("block_threads", C.c_int32),
         ("use_graphs", C.c_int32),
         ("cancel_flag", C.c_void_p),
+        ("strip_rows", C.c_int32),
     ]
 
 
@@ -142,7 +143,7 @@ def current_stream() -> Optional[int]:
 
 def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=20,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
-                 use_graphs=True, cancel_flag=None) -> lbm_options:
+                 use_graphs=True, cancel_flag=None, strip_rows=0) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -154,6 +155,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.block_threads = block_threads
     o.use_graphs = 1 if use_graphs else 0
     o.cancel_flag = cancel_flag
+    o.strip_rows = strip_rows
     return o
 
 
