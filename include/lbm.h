@@ -111,6 +111,32 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
                     int32_t* iterations);
 
 /*
+ * Allocation-free variant of lbm_qsgs, for callers that cannot allocate GPU
+ * memory while they run (for example a host whose device memory is owned by
+ * its own pool allocator, or code under a policy that forbids cudaMalloc and
+ * cudaFree after set-up).  The paper has no counterpart to this entry point:
+ * it only changes where the scratch lives.  It produces the same mask as
+ * lbm_qsgs, written to mask_dev_out, a caller-owned DEVICE buffer of
+ * nx*ny*nz bytes on the current device, enqueued on `stream` (NULL = legacy
+ * default stream); the call returns after the mask is complete.
+ *   - Scratch is a file-scope device array inside the library, sized for at
+ *     most 1,048,576 cells (about 9 MB, held on every GPU that loads the
+ *     library until the process exits).  Larger grids return LBM_ERR_ARG.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (once per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the scratch array and it keeps the last call's contents
+ *     (every value a call reads is written by that call first).  Calls that
+ *     overlap on the GPU -- from several host threads or several streams --
+ *     race on it: serialise them.
+ * Errors are reported like lbm_qsgs's, with detail from lbm_last_error(NULL).
+ */
+lbm_status lbm_qsgs_noalloc(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p,
+                            double porosity, double d_face, void* stream, uint8_t* mask_dev_out,
+                            int32_t* iterations);
+
+/*
  * Create a solver for a batch of n independent domains (Sec. 2's sweeps of
  * tau x resolution x geometry), all D2Q9 (every nz = 1) or all D3Q19 (every
  * nz > 1, or lattice forced by lbm_create_domain_3d).  Per domain: pressure

@@ -240,6 +240,8 @@ lbm_status check_domain(lbm_handle h, int32_t d) {
 
 }  // namespace
 
+void lbmgb::set_thread_error(const std::string& msg) { t_err = msg; }
+
 // ---------------------------------------------------------------------------
 extern "C" {
 

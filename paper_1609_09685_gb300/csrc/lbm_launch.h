@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "lbm_device.cuh"
 
@@ -46,5 +47,8 @@ struct QsgsScratch {
 int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double porosity,
                   double d_face, uint8_t* d_mask, const QsgsScratch& sc, cudaStream_t st,
                   int* iterations, cudaError_t* cuda_err);
+
+// Record the detail string lbm_last_error(NULL) returns on this thread (capi.cu).
+void set_thread_error(const std::string& msg);
 
 }  // namespace lbmgb

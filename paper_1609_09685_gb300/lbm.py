@@ -93,6 +93,7 @@ def load(path: Optional[str] = None):
         "lbm_last_error": (C.c_char_p, [P]),
         "lbm_options_default": (None, [P]),
         "lbm_qsgs": (i32, [u64, i32, i32, i32, d, d, d, P, P, P]),
+        "lbm_qsgs_noalloc": (i32, [u64, i32, i32, i32, d, d, d, P, P, P]),
         "lbm_batch_create": (i32, [i32, P, P, P]),
         "lbm_create_domain": (i32, [P, i32, i32, d, d, P, P]),
         "lbm_create_domain_3d": (i32, [P, i32, i32, i32, d, d, P, P]),
@@ -182,6 +183,20 @@ def lbm_qsgs(seed: int, shape: Sequence[int], core_p: float, porosity: float,
     _check(load().lbm_qsgs(seed & (2**64 - 1), nx, ny, nz, core_p, porosity, d_face, stream,
                            _ptr(out), C.byref(it)))
     return (out[0] if len(shape) == 2 else out), it.value
+
+
+def lbm_qsgs_noalloc(seed: int, shape: Sequence[int], core_p: float, porosity: float,
+                     mask_dev_ptr: int, d_face: float = 0.2, stream=None) -> int:
+    """QSGS mask written to a caller-owned device buffer (device pointer
+    mask_dev_ptr, nx*ny*nz bytes) with no allocation; returns the iteration count."""
+    if len(shape) == 2:
+        nz, (ny, nx) = 1, shape
+    else:
+        nz, ny, nx = shape
+    it = C.c_int32(0)
+    _check(load().lbm_qsgs_noalloc(seed & (2**64 - 1), nx, ny, nz, core_p, porosity, d_face, stream,
+                                   C.c_void_p(int(mask_dev_ptr)), C.byref(it)))
+    return it.value
 
 
 class Solver:
