@@ -48,6 +48,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--ttp", action="store_true",
+                   help="also measure time-to-permeability, batched vs plain (one domain at a time)")
+    p.add_argument("--ttp-sizes", default="400x200",
+                   help="resolutions of the tau sweep used for --ttp, e.g. 400x200,800x400")
+    p.add_argument("--ttp-tol", type=float, default=1e-4)
     return p.parse_args()
 
 
@@ -183,6 +188,71 @@ def oracle_sample(wl, seconds: float):
 
 
 # ---------------------------------------------------------------------------
+# time-to-permeability
+# ---------------------------------------------------------------------------
+def time_to_k(t, k, tol):
+    """First host time after which k(t) stays within tol (relative) of the
+    run's converged value for every later check interval."""
+    if len(k) == 0:
+        return None
+    kf = k[-1]
+    bad = np.where(~(np.abs(k - kf) <= tol * abs(kf)))[0]
+    i = int(bad[-1]) + 1 if len(bad) else 0
+    return float(t[min(i, len(t) - 1)])
+
+
+def measure_ttp(args, lbm, sp):
+    sizes = []
+    for tok in args.ttp_sizes.split(","):
+        nx, ny = (int(v) for v in tok.lower().split("x"))
+        phi = {400: 0.7394, 800: 0.7532, 1200: 0.7578}.get(nx, 0.75)
+        sizes.append((nx, ny, phi))
+    wl = workloads.tau_sweep(sizes=sizes)
+    cache, masks = {}, []
+    for d in wl.domains:
+        key = (d.shape, d.seed, d.porosity)
+        if key not in cache:
+            cache[key], _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity, d.d_face, stream=sp)
+        masks.append(cache[key])
+    taus = [d.tau for d in wl.domains]
+    drhos = [d.drho for d in wl.domains]
+    opts = lbm.make_options(stream=sp)
+    out = {"workload": wl.name, "sizes": args.ttp_sizes, "domains": len(wl.domains), "tol_rel": args.ttp_tol,
+           "residual_tol": wl.tol, "k_reference": "each run's own converged k (r < tol or FP32 stall)"}
+    # batched: all domains in one solver, converged ones retire
+    s = lbm.lbm_batch_create(masks, taus, drhos, opts)
+    t0 = time.perf_counter()
+    rc, st, steps, res = lbm.lbm_run_to_steady(s, wl.tol, wl.max_steps)
+    t_batch = time.perf_counter() - t0
+    kb, _ = lbm.lbm_permeability(s)
+    ttp_b = [time_to_k(lbm.lbm_get_history(s, d)[3], lbm.lbm_get_history(s, d)[1], args.ttp_tol)
+             for d in range(len(masks))]
+    s.close()
+    # plain: one domain at a time
+    ttp_p, t_plain, kp, steps_p = [], 0.0, [], []
+    for d in range(len(masks)):
+        s1 = lbm.lbm_create_domain(masks[d], taus[d], drhos[d], opts)
+        t0 = time.perf_counter()
+        _, st1, stp1, _ = lbm.lbm_run_to_steady(s1, wl.tol, wl.max_steps)
+        t_plain += time.perf_counter() - t0
+        hs = lbm.lbm_get_history(s1, 0)
+        ttp_p.append(time_to_k(hs[3], hs[1], args.ttp_tol))
+        kp.append(float(lbm.lbm_permeability(s1)[0][0]))
+        steps_p.append(int(stp1[0]))
+        s1.close()
+    out.update({
+        "batched_time_to_k_s": max(ttp_b), "plain_time_to_k_s": float(sum(ttp_p)),
+        "batched_stop_s": t_batch, "plain_stop_s": t_plain,
+        "speedup_time_to_k": float(sum(ttp_p)) / max(ttp_b),
+        "max_rel_k_diff_batched_vs_plain": float(np.max(np.abs(np.array(kb) - np.array(kp)) / np.abs(kp))),
+        "per_domain": [{"tau": taus[d], "nx": wl.domains[d].nx, "steps": int(steps[d]),
+                        "status": int(st[d]), "k": float(kb[d]), "ttp_batched_s": ttp_b[d],
+                        "ttp_plain_s": ttp_p[d]} for d in range(len(masks))],
+    })
+    return out
+
+
+# ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -315,6 +385,7 @@ def run_native(args):
         dist.all_reduce(uu)
         t_e2e, e2e_updates = float(tt[0]), float(uu[0])
     s.close()
+    ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
 
     if rank == 0:
         peak, peak_src = measured_hbm_peak()
@@ -350,6 +421,8 @@ def run_native(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if ttp is not None:
+            line["time_to_permeability"] = ttp
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -63,7 +63,7 @@ typedef struct lbm_options {
     int32_t struct_size;     /* sizeof(lbm_options) */
     int32_t equilibrium;     /* LBM_EQ_QUADRATIC (default) or LBM_EQ_LINEAR (Stokes, Sec. 2's 3D case) */
     int32_t check_interval;  /* steps between convergence checks N (default 100, >= 1) */
-    int32_t stall_checks;    /* checks without 10% residual drop before LBM_STALLED (default 20) */
+    int32_t stall_checks;    /* checks without a new minimum residual before LBM_STALLED (default 50) */
     double stall_floor;      /* stall rule applies only while r < stall_floor (default 1e-5) */
     double rho_out;          /* outlet density rho_0 (default 1.0) */
     void* stream;            /* cudaStream_t; NULL = legacy default stream */
@@ -184,9 +184,10 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs);
  * state").  Every check_interval steps the residual
  *   r = sqrt( sum |u^t - u^{t-N}|^2 / sum |u^t|^2 )
  * is formed per domain; a domain with r < tol is converged and retired from
- * further stepping.  Because the state is FP32, a domain whose r stays below
- * stall_floor without falling 10% over stall_checks consecutive checks is
- * retired as LBM_STALLED.  Returns LBM_OK when every domain converged,
+ * further stepping.  Because the state is FP32, r eventually stops decaying
+ * and jitters at a rounding floor: a domain whose r is below stall_floor and
+ * has not set a new minimum for stall_checks consecutive checks is retired as
+ * LBM_STALLED.  Returns LBM_OK when every domain converged,
  * LBM_STALLED when all finished and some stalled, LBM_NOT_CONVERGED when
  * max_steps was reached first, LBM_DIVERGED on a non-finite velocity,
  * LBM_CANCELLED if opt.cancel_flag was raised.  Per-domain arrays (each
@@ -221,6 +222,14 @@ lbm_status lbm_set_populations(lbm_handle h, int32_t d, const double* f);
  */
 lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const float* ux,
                           const float* uy, const float* uz, int32_t on_device);
+
+/* Per-check-interval record of domain d from the last lbm_run_to_steady:
+ * global step counter, permeability k(t) from that interval's flux (as
+ * lbm_permeability), residual r, and host seconds since the call began.  Up to
+ * `capacity` entries are written to each non-null array; *count receives the
+ * number recorded.  Used to judge time-to-permeability a posteriori. */
+lbm_status lbm_get_history(lbm_handle h, int32_t d, int64_t* steps, double* k, double* residual,
+                           double* seconds, int32_t capacity, int32_t* count);
 
 /* Steps taken since creation (the batch's global step counter). */
 lbm_status lbm_get_step(lbm_handle h, int64_t* step);

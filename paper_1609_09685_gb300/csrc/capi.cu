@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,10 @@ struct DomainHost {
     std::vector<double> rhist;
     bool has_obs = false;
     double obs[kNumObs] = {0};
+    // per check interval of the last lbm_run_to_steady: step, k, residual,
+    // host seconds since the call began
+    std::vector<int64_t> h_step;
+    std::vector<double> h_k, h_r, h_t;
 };
 
 struct GraphKey {
@@ -154,6 +159,14 @@ void free_solver(lbm_handle h) {
 }
 
 double knudsen(double tau, int nx) { return std::sqrt(M_PI / 6.0) * (tau - 0.5) / (double)nx; }
+
+// Darcy's law with the mass flow rate (Sec. 2): k = nu <j_x> (nx - 1) / (c_s^2 drho),
+// nu = (tau - 1/2)/3 (Eq. 1), <j_x> the superficial mean over all nodes.
+double darcy_k(const DomainHost& D, double sum_jx) {
+    const double nu = (D.tau - 0.5) / 3.0;
+    const double jmean = sum_jx / ((double)D.nx * D.ny * D.nz);
+    return nu * jmean * (double)(D.nx - 1) / ((1.0 / 3.0) * D.drho);
+}
 
 lbm_status upload_dom(lbm_handle h) {
     for (size_t d = 0; d < h->dom.size(); ++d) h->hdom[d].active = h->dom[d].active;
@@ -272,7 +285,7 @@ void lbm_options_default(lbm_options* o) {
     o->struct_size = (int32_t)sizeof(lbm_options);
     o->equilibrium = LBM_EQ_QUADRATIC;
     o->check_interval = 100;
-    o->stall_checks = 20;
+    o->stall_checks = 50;
     o->stall_floor = 1e-5;
     o->rho_out = 1.0;
     o->stream = nullptr;
@@ -575,9 +588,14 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
         D.steps = 0;
         D.residual = INFINITY;
         D.rhist.clear();
+        D.h_step.clear();
+        D.h_k.clear();
+        D.h_r.clear();
+        D.h_t.clear();
     }
     lbm_status s = upload_dom(h);
     if (s != LBM_OK) return s;
+    const auto t_start = std::chrono::steady_clock::now();
     const int64_t N = h->opt.check_interval;
     int64_t taken = 0;
     size_t nactive = n;
@@ -604,13 +622,24 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
             if (o[2] > 0.0) r = std::sqrt(o[1] / o[2]);
             else r = (o[1] == 0.0) ? 0.0 : INFINITY;
             D.residual = r;
+            D.h_step.push_back(h->step);
+            D.h_k.push_back(D.drho != 0.0 ? darcy_k(D, o[0]) : NAN);
+            D.h_r.push_back(r);
+            D.h_t.push_back(std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
             lbm_status ds = LBM_NOT_CONVERGED;
             if (o[4] > 0.0 || !std::isfinite(o[0])) ds = LBM_DIVERGED;
             else if (r < tol) ds = LBM_OK;
             else {
-                D.rhist.push_back(r);
-                const size_t m = D.rhist.size(), w = (size_t)h->opt.stall_checks;
-                if (r < h->opt.stall_floor && m > w && r > 0.9 * D.rhist[m - 1 - w]) ds = LBM_STALLED;
+                // FP32 floor: below stall_floor the residual jitters instead of
+                // decaying, so it stops setting new minima; a slow but genuine
+                // decay sets one at every check.
+                if (D.rhist.empty() || r < D.rhist[0]) {
+                    D.rhist.assign(1, r);  // rhist[0] = best residual so far
+                } else {
+                    D.rhist.push_back(r);  // checks since the best
+                }
+                if (r < h->opt.stall_floor && (int64_t)D.rhist.size() > (int64_t)h->opt.stall_checks)
+                    ds = LBM_STALLED;
             }
             if (ds != LBM_NOT_CONVERGED) {
                 D.status = ds;
@@ -667,13 +696,11 @@ lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
     lbm_status rs = LBM_OK;
     for (size_t d = 0; d < h->dom.size(); ++d) {
         const DomainHost& D = h->dom[d];
-        const double nu = (D.tau - 0.5) / 3.0;
-        const double jmean = D.obs[0] / ((double)D.nx * D.ny * D.nz);
         if (D.drho == 0.0) {
             k[d] = NAN;
             rs = fail(h, LBM_ERR_ARG, "drho = 0: permeability undefined");
         } else {
-            k[d] = nu * jmean * (double)(D.nx - 1) / ((1.0 / 3.0) * D.drho);
+            k[d] = darcy_k(D, D.obs[0]);
         }
         if (kn) kn[d] = knudsen(D.tau, D.nx);
     }
@@ -768,6 +795,23 @@ lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const floa
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
     h->dom[d].has_obs = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_history(lbm_handle h, int32_t d, int64_t* steps, double* k, double* residual, double* seconds,
+                           int32_t capacity, int32_t* count) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    const DomainHost& D = h->dom[d];
+    const int32_t n = (int32_t)D.h_k.size();
+    if (count) *count = n;
+    const int32_t m = std::min(n, std::max(capacity, 0));
+    for (int32_t i = 0; i < m; ++i) {
+        if (steps) steps[i] = D.h_step[i];
+        if (k) k[i] = D.h_k[i];
+        if (residual) residual[i] = D.h_r[i];
+        if (seconds) seconds[i] = D.h_t[i];
+    }
     return LBM_OK;
 }
 

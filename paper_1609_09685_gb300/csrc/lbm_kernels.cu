@@ -58,6 +58,16 @@ __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
 
 // Zou-He pressure closure in shifted form for the face whose inward normal is
 // `SIDE` (+1 at x = 0, -1 at x = N_x - 1), u_y = u_z = 0:
@@ -197,9 +207,15 @@ struct MinBlocks {
 #endif
 constexpr int kStages = LBM_SC_STAGES;
 
-template <class L>
+// Shared-memory slots per stage: the Q source populations, plus the D
+// components of u_prev when the step also observes.
+template <class L, bool OBS>
+__host__ __device__ constexpr int stage_slots() {
+    return L::Q + (OBS ? L::D : 0);
+}
+template <class L, bool OBS>
 constexpr size_t sc_smem_bytes(int threads) {
-    return (size_t)(threads / 32) * kStages * L::Q * 32 * sizeof(float);
+    return (size_t)(threads / 32) * kStages * stage_slots<L, OBS>() * 32 * sizeof(float);
 }
 
 // A warp walks its strip row by row.  Rows k+1 .. k+S-1 are already in
@@ -237,7 +253,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
     const float ow3[3] = {3.0f * ow[0], 3.0f * ow[1], 3.0f * ow[2]};
     float* const* dst = A.dst;
-    float* wbuf = smem + (size_t)wid * S * Q * 32;
+    constexpr int SL = stage_slots<L, OBS>();
+    float* wbuf = smem + (size_t)wid * S * SL * 32;
     const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(wbuf) + 4u * lane;
     // Window records of planes z-1, z, z+1 and rows clamped onto the domain
     // (the clamped row or plane is the mirror image at a specular face).
@@ -278,8 +295,12 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             constexpr int C = (L::NROW == 9) ? 4 : 1;
             flq[st] = win_fluid<0>(w[C]);
             kdq[st] = win_idx<0>(w[C]);
-            issue_row<L>(A, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sb0 + 4u * (uint32_t)(st * Q * 32),
-                         std::make_integer_sequence<int, Q>{});
+            const uint32_t sbase = sb0 + 4u * (uint32_t)(st * SL * 32);
+            issue_row<L>(A, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase, std::make_integer_sequence<int, Q>{});
+            if (OBS) {
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) cp_async4(sbase + 4u * (32u * (Q + a)), uprev + (size_t)a * PS + kdq[st]);
+            }
             if (next + 1 < nrows) {
 #pragma unroll
                 for (int zi = 0; zi < NZ; ++zi) {
@@ -300,13 +321,15 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     for (int st = 0; st < S - 1; ++st) issue(st);
 
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0;
+    float a0s = 0.f, a1s = 0.f, a2s = 0.f, a5s = 0.f, umax2 = 0.f;
+    int nbad = 0;
     for (int k = 0; k < nrows; k += S) {
 #pragma unroll
         for (int st = 0; st < S; ++st) {
             if (k + st >= nrows) break;
             issue((st + S - 1) % S);
             cp_async_wait<S - 1>();
-            const float* sf = wbuf + st * Q * 32 + lane;
+            const float* sf = wbuf + st * SL * 32 + lane;
             float f[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = sf[i * 32];
@@ -352,17 +375,20 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     dst[o][kk] = fmaf(omc, f[o], sym - anti);
                 }
                 if (OBS) {
+                    // Within one strip (at most 8 rows x 32 lanes) the sums are
+                    // FP32 -- the FP64 rate of this part is low -- and each
+                    // strip hands one FP64 partial to the cross-strip FP64 pass.
                     const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
-                    const float px = uprev[kk], py = uprev[PS + kk];
-                    const float pz = (L::D == 3) ? uprev[2u * PS + kk] : 0.f;
+                    const float px = sf[Q * 32], py = sf[(Q + 1) * 32];
+                    const float pz = (L::D == 3) ? sf[(Q + 2) * 32] : 0.f;
                     const float ex = ux - px, ey = uy - py, ez = uz - pz;
-                    const double u2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-                    v0 += (double)jx;
-                    v1 += (double)ex * ex + (double)ey * ey + (double)ez * ez;
-                    v2 += u2;
-                    v3 = fmax(v3, sqrt(u2));
-                    v4 += (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? 0.0 : 1.0;
-                    v5 += (double)dr;
+                    const float uu = ux * ux + uy * uy + uz * uz;
+                    a0s += jx;
+                    a1s += ex * ex + ey * ey + ez * ez;
+                    a2s += uu;
+                    umax2 = fmaxf(umax2, uu);
+                    nbad += (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? 0 : 1;
+                    a5s += dr;
                     uprev[kk] = ux;
                     uprev[PS + kk] = uy;
                     if (L::D == 3) uprev[2u * PS + kk] = uz;
@@ -372,12 +398,18 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     }
     cp_async_wait<0>();
     if (OBS) {
-        v0 = warp_sum(v0);
-        v1 = warp_sum(v1);
-        v2 = warp_sum(v2);
-        v3 = warp_max(v3);
-        v4 = warp_sum(v4);
-        v5 = warp_sum(v5);
+        a0s = warp_sumf(a0s);
+        a1s = warp_sumf(a1s);
+        a2s = warp_sumf(a2s);
+        a5s = warp_sumf(a5s);
+        umax2 = warp_maxf(umax2);
+        nbad = __reduce_add_sync(kFull, nbad);
+        v0 = a0s;
+        v1 = a1s;
+        v2 = a2s;
+        v3 = sqrt((double)umax2);
+        v4 = (double)nbad;
+        v5 = a5s;
         if (lane == 0) {
             double* p = partials + (size_t)item * kNumObs;
             p[0] = v0;
@@ -747,11 +779,12 @@ inline unsigned seg_blocks(uint32_t nseg, int threads) {
 template <class L, int EQ, bool OBS>
 static cudaError_t sc_launch(unsigned nb, int threads, const HotArgs& A, float* uprev, double* partials,
                              cudaStream_t st) {
-    const size_t sm = sc_smem_bytes<L>(threads);
+    const size_t sm = sc_smem_bytes<L, OBS>(threads);
     static bool attr_set = false;  // per template instance; the attribute is per device function
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_stream_collide<L, EQ, OBS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem_bytes<L>(256));
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sc_smem_bytes<L, OBS>(256));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

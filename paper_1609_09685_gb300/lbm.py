@@ -109,6 +109,7 @@ def load(path: Optional[str] = None):
         "lbm_set_populations": (i32, [P, i32, P]),
         "lbm_set_fields": (i32, [P, i32, P, P, P, P, i32]),
         "lbm_get_step": (i32, [P, P]),
+        "lbm_get_history": (i32, [P, i32, P, P, P, P, i32, P]),
         "lbm_save": (i32, [P, C.c_char_p]),
         "lbm_load": (i32, [C.c_char_p, P, P]),
     }
@@ -142,7 +143,7 @@ def current_stream() -> Optional[int]:
     return None
 
 
-def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=20,
+def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=50,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0) -> lbm_options:
     o = lbm_options()
@@ -347,6 +348,20 @@ def lbm_set_fields(s: Solver, d: int, drho, ux, uy, uz=None, on_device: bool = F
             raise ValueError("field shape mismatch")
     _check(load().lbm_set_fields(s.handle, d, *[None if a is None else _ptr(a) for a in arrs], 0),
            s.handle)
+
+
+def lbm_get_history(s: Solver, d: int = 0):
+    """(steps, k, residual, seconds) per check interval of the last run_to_steady."""
+    cnt = C.c_int32(0)
+    _check(load().lbm_get_history(s.handle, d, None, None, None, None, 0, C.byref(cnt)), s.handle)
+    n = cnt.value
+    st = np.zeros(n, np.int64)
+    k = np.zeros(n, np.float64)
+    r = np.zeros(n, np.float64)
+    t = np.zeros(n, np.float64)
+    _check(load().lbm_get_history(s.handle, d, _ptr(st), _ptr(k), _ptr(r), _ptr(t), n, C.byref(cnt)),
+           s.handle)
+    return st, k, r, t
 
 
 def lbm_get_step(s: Solver) -> int:
