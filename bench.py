@@ -53,6 +53,12 @@ def parse():
     p.add_argument("--ttp-sizes", default="400x200",
                    help="resolutions of the tau sweep used for --ttp, e.g. 400x200,800x400")
     p.add_argument("--ttp-tol", type=float, default=1e-4)
+    p.add_argument("--warmstart", action="store_true",
+                   help="also train the U-Net warm start and compare time-to-permeability on held-out domains")
+    p.add_argument("--ws-train", type=int, default=256, help="training solutions (512x256 domains)")
+    p.add_argument("--ws-eval", type=int, default=16, help="held-out evaluation domains")
+    p.add_argument("--ws-epochs", type=int, default=30)
+    p.add_argument("--ws-shape", default="256x512", help="ny x nx of the warm-start domains")
     return p.parse_args()
 
 
@@ -252,6 +258,48 @@ def measure_ttp(args, lbm, sp):
     return out
 
 
+def measure_warmstart(args, lbm, sp):
+    """Time-to-permeability on held-out domains: plain (one domain at a time,
+    equilibrium start), batched (equilibrium start), batched + learned warm start."""
+    from paper_1609_09685_gb300 import warmstart as WS
+    ny, nx = (int(v) for v in args.ws_shape.lower().split("x"))
+    shape = (ny, nx)
+    t0 = time.perf_counter()
+    ds = WS.generate(WS.make_domains(args.ws_train, shape, seed0=0, master_seed=11), shape)
+    t_gen = time.perf_counter() - t0
+    ev = WS.generate(WS.make_domains(args.ws_eval, shape, seed0=1_000_000, master_seed=12), shape)
+    levels = 8 if min(ny, nx) % 128 == 0 else 4
+    chans = (16, 32, 32, 64, 64, 128, 128, 128)[:levels]
+    net = WS.UNet(chans, seed=0)
+    t0 = time.perf_counter()
+    hist = WS.train(net, ds, epochs=args.ws_epochs, batch=8, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    res = WS.evaluate(net, ev)
+    # plain: one domain at a time from the equilibrium start
+    plain_t, plain_steps = [], []
+    for d in range(len(ev)):
+        s1 = lbm.lbm_create_domain(ev.masks_host[d], ev.taus[d], ev.drhos[d], lbm.make_options())
+        lbm.lbm_run_to_steady(s1, 1e-9, 400_000)
+        stp, kk, rr, tt = lbm.lbm_get_history(s1, 0)
+        tk, ik = WS.time_to_k(tt, kk, args.ttp_tol)
+        plain_t.append(tk)
+        plain_steps.append(int(stp[ik]))
+        s1.close()
+    eq, wm = res["equilibrium"], res["warm"]
+    return {
+        "shape": [ny, nx], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
+        "unet_params": int(net.nparams), "epochs": args.ws_epochs, "loss_first_last": [hist[0], hist[-1]],
+        "datagen_s": t_gen, "train_s": t_train, "tol_rel": args.ttp_tol,
+        "plain_time_to_k_s": float(sum(plain_t)), "plain_steps_to_k": int(sum(plain_steps)),
+        "batched_time_to_k_s": res["time_to_all_k_equilibrium_s"],
+        "batched_warm_time_to_k_s": res["time_to_all_k_warm_s"],
+        "batched_steps_to_k": res["steps_to_k_equilibrium"], "batched_warm_steps_to_k": res["steps_to_k_warm"],
+        "warm_predict_s": wm["predict_s"], "k_rel_diff_warm_vs_equilibrium_max": res["k_rel_diff_max"],
+        "per_domain_steps_to_k": {"equilibrium": [p["steps_to_k"] for p in eq["per_domain"]],
+                                  "warm": [p["steps_to_k"] for p in wm["per_domain"]]},
+    }
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -386,6 +434,7 @@ def run_native(args):
         t_e2e, e2e_updates = float(tt[0]), float(uu[0])
     s.close()
     ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
+    ws = measure_warmstart(args, lbm, sp) if (args.warmstart and rank == 0) else None
 
     if rank == 0:
         peak, peak_src = measured_hbm_peak()
@@ -423,6 +472,8 @@ def run_native(args):
             line["cpu_baseline"] = cpu
         if ttp is not None:
             line["time_to_permeability"] = ttp
+        if ws is not None:
+            line["warm_start"] = ws
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -63,7 +63,7 @@ typedef struct lbm_options {
     int32_t struct_size;     /* sizeof(lbm_options) */
     int32_t equilibrium;     /* LBM_EQ_QUADRATIC (default) or LBM_EQ_LINEAR (Stokes, Sec. 2's 3D case) */
     int32_t check_interval;  /* steps between convergence checks N (default 100, >= 1) */
-    int32_t stall_checks;    /* checks without a new minimum residual before LBM_STALLED (default 50) */
+    int32_t stall_checks;    /* checks without a new minimum residual before LBM_STALLED (default 200) */
     double stall_floor;      /* stall rule applies only while r < stall_floor (default 1e-5) */
     double rho_out;          /* outlet density rho_0 (default 1.0) */
     void* stream;            /* cudaStream_t; NULL = legacy default stream */
@@ -71,6 +71,7 @@ typedef struct lbm_options {
     int32_t use_graphs;      /* capture each check interval as a CUDA graph (default 1) */
     volatile const int32_t* cancel_flag; /* host flag polled between intervals; nonzero cancels */
     int32_t strip_rows;      /* rows per stream-collide work item (0 = default 8, max 255) */
+    double k_tol;            /* permeability-based stop (see lbm_run_to_steady); 0 disables (default 1e-5) */
 } lbm_options;
 
 /* One domain of a batch. */
@@ -167,13 +168,16 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 
 /*
  * Enqueue nsteps steps of which the last also reduces, per domain, in FP64:
- *   obs[d*8 + 0] = sum of j_x over fluid nodes (mass flux, Eq. 2's sum)
+ *   obs[d*8 + 0] = sum over the N_x - 1 interior planes x + 1/2 of the mass
+ *                  crossing each plane in the next streaming (the link flux
+ *                  of the post-collision populations); /(N_x - 1) = mass flow rate
  *   obs[d*8 + 1] = sum |u - u_prev|^2   (u_prev = u at the previous observation)
  *   obs[d*8 + 2] = sum |u|^2
  *   obs[d*8 + 3] = max |u|
  *   obs[d*8 + 4] = count of nodes with a non-finite velocity
  *   obs[d*8 + 5] = sum of (rho - rho_0)
- *   obs[d*8 + 6..7] = 0 (reserved)
+ *   obs[d*8 + 6] = sum of j_x over fluid nodes (node momentum, a diagnostic)
+ *   obs[d*8 + 7] = 0 (reserved)
  * and stores u as the new u_prev.  nsteps = 0 observes the current state
  * without stepping.  obs: host, 8*n doubles; the call synchronises.
  */
@@ -184,10 +188,20 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs);
  * state").  Every check_interval steps the residual
  *   r = sqrt( sum |u^t - u^{t-N}|^2 / sum |u^t|^2 )
  * is formed per domain; a domain with r < tol is converged and retired from
- * further stepping.  Because the state is FP32, r eventually stops decaying
+ * further stepping.  A domain is also converged (LBM_OK) when its permeability
+ * k(t), from the FP64 mass flow rate of each check, has settled: over windows
+ * of 5 checks, with D1 and D0 the last two changes of k and q = |D1/D0|, the
+ * remaining error of a geometric approach is at most |D1| q/(1 - q); the
+ * domain stops once that bound is below opt.k_tol |k| at 5 consecutive checks,
+ * or once k has stayed within 0.05 opt.k_tol |k| over 40 checks (|k| is taken
+ * as at least 1e-3 of its largest value in the run, so that a domain whose
+ * flow dies out, having no through-path, stops too).  This is the
+ * stop that matters in FP32: in the Stokes regime the per-node residual
+ * reaches its rounding floor long before the mass flow rate does.  Because the state is FP32, r eventually stops decaying
  * and jitters at a rounding floor: a domain whose r is below stall_floor and
  * has not set a new minimum for stall_checks consecutive checks is retired as
- * LBM_STALLED.  Returns LBM_OK when every domain converged,
+ * LBM_STALLED (a residual more than 30x above the minimum so far counts as a
+ * transient and restarts the count).  Returns LBM_OK when every domain converged,
  * LBM_STALLED when all finished and some stalled, LBM_NOT_CONVERGED when
  * max_steps was reached first, LBM_DIVERGED on a non-finite velocity,
  * LBM_CANCELLED if opt.cancel_flag was raised.  Per-domain arrays (each
@@ -197,9 +211,12 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps,
                              lbm_status* status, int64_t* steps, double* residual);
 
 /*
- * Darcy permeability of each domain from its last observed mass flux (Sec. 2):
- *   k = nu <j_x> (nx - 1) / (c_s^2 drho),  nu = (tau - 1/2)/3 (Eq. 1),
- *   <j_x> = sum of j_x over fluid nodes / (nx ny nz)   (superficial, as Eq. 2)
+ * Darcy permeability of each domain from its last observed mass flow rate
+ * (Sec. 2, "Darcy law with simulated mass flow rate"):
+ *   k = nu <J> (nx - 1) / (ny nz c_s^2 drho),  nu = (tau - 1/2)/3 (Eq. 1),
+ *   <J> = the mass crossing an interior x plane per step, averaged over the
+ *   nx - 1 planes (obs slot 0 / (nx - 1)).  Fluid off the through-paths (closed
+ *   pockets, boundary nodes boxed in by solid) carries no such flux.
  * and Kn = sqrt(pi/6) (tau - 1/2) / nx (Sec. 2).  If no observation exists yet
  * the current state is observed first.  k, kn: host arrays of n (kn nullable).
  */
@@ -238,6 +255,86 @@ lbm_status lbm_get_step(lbm_handle h, int64_t* step);
  * per-domain run state; lbm_load restores a solver that continues bit for bit. */
 lbm_status lbm_save(lbm_handle h, const char* path);
 lbm_status lbm_load(const char* path, const lbm_options* opt, lbm_handle* out);
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (U-Net).                                               */
+/* ------------------------------------------------------------------------ */
+/*
+ * The network maps a 2D mask, x / (nx - 1) and (tau - 1/2) to the normalised
+ * steady fields: the density's deviation from the linear inlet-to-outlet ramp,
+ * (rho - rho_out)/drho - (1 - x/(nx - 1)), and u nu (nx - 1)/(c_s^2 drho).  In the
+ * Stokes regime of Sec. 2 these depend on the geometry (and weakly on tau)
+ * only.  Its prediction only initialises the populations; the lattice
+ * Boltzmann iteration (Sec. 2) then converges from there, so the network
+ * changes how fast the steady state is reached, not what it is.  The paper has
+ * no learned component; this is the acceleration layer built on it.
+ *
+ * Tensor conventions: NHWC, H = ny rows, W = nx columns.  Activations and
+ * gradients are bf16 with channel counts that are multiples of 16.  Weights
+ * are bf16 [taps][cout][cin] (taps = 9 for 3x3 with zero padding, 1 for 1x1),
+ * with an FP32 master copy for the optimiser; biases are FP32.  All pointers
+ * are DEVICE pointers, 16-byte aligned, owned by the caller.  Work is enqueued
+ * on `stream` (NULL = legacy default stream) and nothing is synchronised.
+ * Shapes are validated before any launch (LBM_ERR_ARG); launch failures
+ * return LBM_ERR_CUDA.  Details come from lbm_last_error(NULL).
+ */
+
+/* out = act(b + sum_{tap, ci} in[p + off_tap, ci] w[tap][co][ci]), act = ReLU if
+ * relu != 0.  BF16 tensor-core implicit GEMM (mma.sync m16n8k16), FP32
+ * accumulation.  bias and out_f32 (an FP32 copy of out) may be NULL. */
+lbm_status lbm_nn_conv_fwd(const void* in, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wts,
+                           const float* bias, int32_t taps, int32_t cout, int32_t relu, void* out,
+                           float* out_f32, void* stream);
+/* gin = adjoint of the convolution applied to gout (no activation).
+ * wflip_scratch: taps*cin*cout bf16. */
+lbm_status lbm_nn_conv_bwd_data(const void* gout, int32_t n, int32_t h, int32_t w, int32_t cout,
+                                const void* wts, int32_t taps, int32_t cin, void* wflip_scratch,
+                                void* gin, void* stream);
+/* dw[tap][co][ci] (+)= sum_p gout[p, co] in[p + off_tap, ci], db[co] (+)= sum_p gout[p, co]
+ * (FP32; accumulate != 0 adds to dw/db).  scratch: FP32 partial sums; at least
+ * taps*cout*cin + cout floats, more allows more parallel blocks.  db may be NULL. */
+lbm_status lbm_nn_conv_bwd_weight(const void* in, const void* gout, int32_t n, int32_t h, int32_t w,
+                                  int32_t cin, int32_t cout, int32_t taps, float* dw, float* db,
+                                  int32_t accumulate, float* scratch, size_t scratch_floats, void* stream);
+/* gx = gy where y > 0, else 0 (gradient through a ReLU with output y). */
+lbm_status lbm_nn_relu_bwd(const void* y, const void* gy, void* gx, size_t count, void* stream);
+/* 2x2 average pooling of an h x w input (h, w even) and its adjoint. */
+lbm_status lbm_nn_pool2_fwd(const void* in, int32_t n, int32_t h, int32_t w, int32_t c, void* out, void* stream);
+lbm_status lbm_nn_pool2_bwd(const void* gout, int32_t n, int32_t h, int32_t w, int32_t c, void* gin,
+                            void* stream);
+/* Nearest-neighbour 2x upsampling of an h x w input and its adjoint. */
+lbm_status lbm_nn_up2_fwd(const void* in, int32_t n, int32_t h, int32_t w, int32_t c, void* out, void* stream);
+lbm_status lbm_nn_up2_bwd(const void* gout, int32_t n, int32_t h, int32_t w, int32_t c, void* gin, void* stream);
+/* dst[p, dc0 + c] = src[p, sc0 + c] for c < nc over npix pixels (channel
+ * concatenation and its adjoint); sld/dld are the channel strides. */
+lbm_status lbm_nn_copy_channels(const void* src, int32_t sld, int32_t sc0, void* dst, int32_t dld, int32_t dc0,
+                                int32_t nc, size_t npix, void* stream);
+/* Masked mean squared error over fluid pixels (solid[p] == 0) and the first
+ * nout channels, scaled by inv_count: *loss (device) = inv_count * sum d^2 and
+ * grad = 2 d inv_count (bf16, stride ld; zero on solids and padding channels;
+ * grad may be NULL).  target: FP32 [npix][nout].  scratch256: 256 floats. */
+lbm_status lbm_nn_mse(const void* pred, int32_t ld, const float* target, const uint8_t* solid, size_t npix,
+                      int32_t nout, float inv_count, void* grad, float* scratch256, float* loss, void* stream);
+/* AdamW step (bias-corrected, decoupled weight decay) on FP32 parameters;
+ * refreshes the bf16 copy p_bf16 when non-NULL.  step >= 1. */
+lbm_status lbm_nn_adamw(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,
+                        float eps, float wd, int32_t step, void* p_bf16, void* stream);
+/* out = a + b elementwise (bf16; used to merge gradients of a tensor read twice). */
+lbm_status lbm_nn_add(const void* a, const void* b, void* out, size_t n, void* stream);
+/* b = bf16(a) elementwise. */
+lbm_status lbm_nn_f32_to_bf16(const float* a, void* b, size_t n, void* stream);
+/* Network input of one h x w sample: channel 0 = solid flag, 1 = x / (w - 1),
+ * 2 = tau_feat, 3..15 = 0 (bf16, 16 channels). */
+lbm_status lbm_nn_make_input(const uint8_t* solid, int32_t h, int32_t w, float tau_feat, void* out, void* stream);
+/* Training targets from 2D domain d's current populations (on the solver's
+ * stream): out_dev FP32 [ny*nx][3] = ((rho - rho_out)/drho - (1 - x/(nx-1)),
+ * u_x s, u_y s) with s = nu (nx - 1)/(c_s^2 drho); zero on solids. */
+lbm_status lbm_nn_targets(lbm_handle h, int32_t d, float* out_dev);
+/* Warm start of 2D domain d from a normalised prediction pred_dev (bf16
+ * [ny*nx][ld], channels 0..2 as in lbm_nn_targets): populations = g_eq of
+ * rho = rho_out + drho (p0 + 1 - x/(nx-1)) and u = (p1, p2)/s, |u| clipped to
+ * 0.1 c_s. */
+lbm_status lbm_warm_start(lbm_handle h, int32_t d, const void* pred_dev, int32_t ld);
 
 #ifdef __cplusplus
 }

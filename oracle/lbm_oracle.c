@@ -26,8 +26,8 @@
  *     1997 pressure condition; in 3D the Hecht & Harting 2010 form), symmetric
  *     boundary at top/bottom (read as specular reflection), solids by halfway
  *     bounce-back (the paper is silent on the wall rule).
- *   - Sec. 2: permeability from the mass flow rate by Darcy's law, with the
- *     superficial average over all N_grid nodes as in Eq. (2).
+ *   - Sec. 2: permeability from the mass flow rate (the link flux through the
+ *     cross-section planes) by Darcy's law.
  *   - Sec. 2: Kn = sqrt(pi/6) (tau - 1/2) / N_x.
  *   - Sec. 2 ("randomly generated quartet structure"): QSGS (Wang et al. 2007)
  *     growth of the solid phase driven by a counter-based splitmix64 hash
@@ -360,14 +360,32 @@ double oc_mean_jx(int q, int nx, int ny, int nz, const uint8_t* solid, const dou
     return sum / (double)nn;
 }
 
-/* Darcy's law with the mass flow rate: k = nu <j_x> L / (c_s^2 (rho_in - rho_out)),
- * nu = (tau - 1/2)/3 (Eq. 1), L = N_x - 1 (distance between the two imposed
- * pressure columns), c_s^2 = 1/3. */
+int oc_link_flux(int q, int nx, int ny, int nz, const uint8_t* solid, const double* f, double* jplane);
+
+/* Sec. 2: the permeability follows from Darcy's law with the simulated mass
+ * flow rate.  The mass flow rate is the mass crossing a cross-section per step:
+ * the link flux J_{x+1/2} through the plane between columns x and x+1, averaged
+ * over the N_x - 1 interior planes (at steady state it is the same on every
+ * plane).  With the superficial velocity U = J / (rho A), A = N_y N_z, the
+ * dynamic viscosity mu = rho nu (Eq. 1, nu = (tau - 1/2)/3), the pressure drop
+ * c_s^2 (rho_in - rho_out) over the length L = N_x - 1 between the imposed
+ * pressures, Darcy's U = (k / mu) dP / L gives
+ *   k = nu <J> (N_x - 1) / (A c_s^2 (rho_in - rho_out)).
+ * Fluid that is not on a through-path (closed pockets, boundary nodes boxed
+ * in by solid) carries no link flux across the planes, so it cannot bias k. */
 double oc_permeability(int q, int nx, int ny, int nz, const uint8_t* solid, const double* f,
                        double tau, double rho_in, double rho_out) {
     double nu = (tau - 0.5) / 3.0;
-    double jx = oc_mean_jx(q, nx, ny, nz, solid, f);
-    return nu * jx * (double)(nx - 1) / ((1.0 / 3.0) * (rho_in - rho_out));
+    double* J = (double*)malloc(sizeof(double) * (size_t)(nx - 1));
+    if (!J || oc_link_flux(q, nx, ny, nz, solid, f, J)) {
+        free(J);
+        return NAN;
+    }
+    double sum = 0.0;
+    for (int x = 0; x + 1 < nx; ++x) sum += J[x];
+    free(J);
+    double jmean = sum / (double)(nx - 1);
+    return nu * jmean * (double)(nx - 1) / ((double)ny * (double)nz * (1.0 / 3.0) * (rho_in - rho_out));
 }
 
 /* Sec. 2: Kn = sqrt(pi/6) (tau - 1/2) / N_x. */

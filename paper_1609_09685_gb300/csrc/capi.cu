@@ -39,6 +39,9 @@ struct DomainHost {
     int64_t steps = 0;
     double residual = INFINITY;
     std::vector<double> rhist;
+    std::vector<double> kq;   // recent k values for the k-based stop
+    int32_t k_ok = 0;         // consecutive checks meeting the k-based stop
+    double k_peak = 0.0;      // largest |k| seen in this run
     bool has_obs = false;
     double obs[kNumObs] = {0};
     // per check interval of the last lbm_run_to_steady: step, k, residual,
@@ -160,12 +163,15 @@ void free_solver(lbm_handle h) {
 
 double knudsen(double tau, int nx) { return std::sqrt(M_PI / 6.0) * (tau - 0.5) / (double)nx; }
 
-// Darcy's law with the mass flow rate (Sec. 2): k = nu <j_x> (nx - 1) / (c_s^2 drho),
-// nu = (tau - 1/2)/3 (Eq. 1), <j_x> the superficial mean over all nodes.
-double darcy_k(const DomainHost& D, double sum_jx) {
+// Darcy's law with the simulated mass flow rate (Sec. 2).  sum_link is the
+// mass crossing the N_x - 1 interior x planes in one step, summed over the
+// planes; its plane average <J> = sum_link / (N_x - 1) is the mass flow rate,
+// U = <J> / (rho A) with A = N_y N_z, mu = rho nu, nu = (tau - 1/2)/3 (Eq. 1),
+// dP = c_s^2 drho over L = N_x - 1:  k = nu <J> (N_x - 1) / (A c_s^2 drho).
+double darcy_k(const DomainHost& D, double sum_link) {
     const double nu = (D.tau - 0.5) / 3.0;
-    const double jmean = sum_jx / ((double)D.nx * D.ny * D.nz);
-    return nu * jmean * (double)(D.nx - 1) / ((1.0 / 3.0) * D.drho);
+    const double jmean = sum_link / (double)(D.nx - 1);
+    return nu * jmean * (double)(D.nx - 1) / ((double)D.ny * D.nz * (1.0 / 3.0) * D.drho);
 }
 
 lbm_status upload_dom(lbm_handle h) {
@@ -234,6 +240,45 @@ void store_obs(lbm_handle h) {
 
 // Copy a retired domain's populations into the other buffer so both hold its
 // final state (no kernel writes a retired domain).
+// Permeability-based stop.  The domain-summed FP64 flux averages out most of
+// the FP32 rounding that makes the per-node residual jitter, so k(t) converges
+// smoothly until a small jitter floor.  Over windows of W = 5 checks, the
+// changes D1 = k_i - k_(i-W) and D0 = k_(i-W) - k_(i-2W) of a geometric approach
+// shrink by q = |D1 / D0| per window and the remaining error is at most
+// |D1| q / (1 - q).  The domain stops once that bound is below k_tol |k| at 5
+// consecutive checks, or once k has stayed within 0.05 k_tol |k| over the last
+// 40 checks (the jitter floor, where the ratio carries no information).  The
+// scale of the tolerance is |k|, but at least 1e-3 of the largest |k| of the run,
+// so that a domain whose flow dies out (no through-path) also stops.
+bool k_converged(DomainHost& D, double k, double k_tol) {
+    D.kq.push_back(k);
+    if (D.kq.size() > 41) D.kq.erase(D.kq.begin());
+    const size_t n = D.kq.size();
+    D.k_peak = std::max(D.k_peak, std::fabs(k));
+    const double tolk = k_tol * std::max(std::fabs(k), 1e-3 * D.k_peak);
+    bool ok = false;
+    if (n >= 11) {
+        const double d1 = D.kq[n - 1] - D.kq[n - 6], d0 = D.kq[n - 6] - D.kq[n - 11];
+        if (d0 != 0.0) {
+            const double q = std::fabs(d1 / d0);
+            if (q < 1.0) ok = std::fabs(d1) * q / (1.0 - q) < tolk;
+        } else {
+            ok = (d1 == 0.0);
+        }
+    }
+    D.k_ok = ok ? D.k_ok + 1 : 0;
+    if (D.k_ok >= 5) return true;
+    if (n == 41) {
+        double lo = D.kq[0], hi = D.kq[0];
+        for (double v : D.kq) {
+            lo = std::min(lo, v);
+            hi = std::max(hi, v);
+        }
+        if (hi - lo < 0.05 * tolk) return true;
+    }
+    return false;
+}
+
 lbm_status mirror_domain(lbm_handle h, size_t d) {
     const DomainHost& D = h->dom[d];
     if (D.fluid_count == 0) return LBM_OK;
@@ -285,7 +330,7 @@ void lbm_options_default(lbm_options* o) {
     o->struct_size = (int32_t)sizeof(lbm_options);
     o->equilibrium = LBM_EQ_QUADRATIC;
     o->check_interval = 100;
-    o->stall_checks = 50;
+    o->stall_checks = 200;
     o->stall_floor = 1e-5;
     o->rho_out = 1.0;
     o->stream = nullptr;
@@ -293,6 +338,7 @@ void lbm_options_default(lbm_options* o) {
     o->use_graphs = 1;
     o->cancel_flag = nullptr;
     o->strip_rows = 0;
+    o->k_tol = 1e-5;
 }
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
@@ -349,7 +395,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
             return fail(nullptr, LBM_ERR_ARG, "lbm_options.struct_size mismatch");
         o = *opt;
     }
-    if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) ||
+    if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) || !(o.k_tol >= 0.0) ||
         (o.equilibrium != LBM_EQ_QUADRATIC && o.equilibrium != LBM_EQ_LINEAR) || o.block_threads < 0 ||
         o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255)
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
@@ -588,6 +634,9 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
         D.steps = 0;
         D.residual = INFINITY;
         D.rhist.clear();
+        D.kq.clear();
+        D.k_ok = 0;
+        D.k_peak = 0.0;
         D.h_step.clear();
         D.h_k.clear();
         D.h_r.clear();
@@ -627,14 +676,18 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
             D.h_r.push_back(r);
             D.h_t.push_back(std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
             lbm_status ds = LBM_NOT_CONVERGED;
+            const double kt = D.h_k.back();
             if (o[4] > 0.0 || !std::isfinite(o[0])) ds = LBM_DIVERGED;
             else if (r < tol) ds = LBM_OK;
+            else if (h->opt.k_tol > 0.0 && std::isfinite(kt) && k_converged(D, kt, h->opt.k_tol)) ds = LBM_OK;
             else {
                 // FP32 floor: below stall_floor the residual jitters instead of
                 // decaying, so it stops setting new minima; a slow but genuine
-                // decay sets one at every check.
-                if (D.rhist.empty() || r < D.rhist[0]) {
-                    D.rhist.assign(1, r);  // rhist[0] = best residual so far
+                // decay sets one at every check.  A residual far above the
+                // best so far is a transient (e.g. after a warm start, whose
+                // first interval barely moves u) and restarts the count.
+                if (D.rhist.empty() || r < D.rhist[0] || r > 30.0 * D.rhist[0]) {
+                    D.rhist.assign(1, r);  // rhist[0] = best residual since the last restart
                 } else {
                     D.rhist.push_back(r);  // checks since the best
                 }
@@ -812,6 +865,35 @@ lbm_status lbm_get_history(lbm_handle h, int32_t d, int64_t* steps, double* k, d
         if (residual) residual[i] = D.h_r[i];
         if (seconds) seconds[i] = D.h_t[i];
     }
+    return LBM_OK;
+}
+
+// nu (N_x - 1) / (c_s^2 drho): the velocity scale of the warm-start targets.
+static double target_u_scale(const DomainHost& D) { return (D.tau - 0.5) / 3.0 * (double)(D.nx - 1) / (D.drho / 3.0); }
+
+lbm_status lbm_nn_targets(lbm_handle h, int32_t d, float* out_dev) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!out_dev) return fail(h, LBM_ERR_ARG, "null output");
+    if (h->q != 9) return fail(h, LBM_ERR_ARG, "warm-start targets are defined for 2D (D2Q9) domains");
+    const DomainHost& D = h->dom[d];
+    if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: targets undefined");
+    CK(h, launch_export_targets(h->geom(), D.seg_begin, D.nseg, h->opt.rho_out, 1.0 / D.drho, target_u_scale(D),
+                                h->d_g[h->cur], out_dev, h->st));
+    return LBM_OK;
+}
+
+lbm_status lbm_warm_start(lbm_handle h, int32_t d, const void* pred_dev, int32_t ld) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!pred_dev || ld < 3) return fail(h, LBM_ERR_ARG, "need a prediction with at least 3 channels");
+    if (h->q != 9) return fail(h, LBM_ERR_ARG, "the warm start is defined for 2D (D2Q9) domains");
+    DomainHost& D = h->dom[d];
+    if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: nothing to predict");
+    const double umax = 0.1 / std::sqrt(3.0);  // |u| <= 0.1 c_s
+    CK(h, launch_warm_start(h->eq, h->geom(), D.seg_begin, D.nseg, pred_dev, ld, (float)D.drho,
+                            (float)(1.0 / target_u_scale(D)), (float)umax, h->d_g[h->cur], h->d_uprev, h->st));
+    D.has_obs = false;
     return LBM_OK;
 }
 

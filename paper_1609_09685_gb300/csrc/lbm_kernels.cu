@@ -21,6 +21,8 @@
 //   equilibrium with relaxation 1/tau.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include <utility>
 
 #include "lbm_device.cuh"
@@ -164,6 +166,14 @@ __device__ __forceinline__ const float* src_ptr(const HotArgs& A, const Win (&w)
     return sf ? plane + win_idx<d::cx>(wn) : A.src[d::o] + kd;
 }
 
+// Bit i set when the pull source of direction i is fluid.  The destination of
+// direction i is the source of opp(i), so bit opp(i) tells whether a
+// post-collision population in direction i reaches a fluid node.
+template <class L, int... Is>
+__device__ __forceinline__ uint32_t src_fluid_mask(const Win (&w)[L::NROW], std::integer_sequence<int, Is...>) {
+    return ((win_fluid<Dir<Is, L>::cx>(w[Dir<Is, L>::row]) ? (1u << Is) : 0u) | ...);
+}
+
 __device__ __forceinline__ void cp_async4(uint32_t saddr, const float* g) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
 }
@@ -282,6 +292,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     int next = 0;  // next row (relative to y0) to issue
     bool flq[S];
     uint32_t kdq[S];
+    uint32_t sfq[S];  // source-fluid masks (observing step only)
     // issue row `next` into stage st, then slide the windows one row down
     auto issue = [&](int st) {
         if (next < nrows) {
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             constexpr int C = (L::NROW == 9) ? 4 : 1;
             flq[st] = win_fluid<0>(w[C]);
             kdq[st] = win_idx<0>(w[C]);
+            sfq[st] = OBS ? src_fluid_mask<L>(w, std::make_integer_sequence<int, Q>{}) : 0u;
             const uint32_t sbase = sb0 + 4u * (uint32_t)(st * SL * 32);
             issue_row<L>(A, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase, std::make_integer_sequence<int, Q>{});
             if (OBS) {
@@ -313,6 +325,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
         } else {
             flq[st] = false;
             kdq[st] = 0u;
+            sfq[st] = 0u;
         }
         ++next;
         cp_async_commit();
@@ -321,7 +334,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     for (int st = 0; st < S - 1; ++st) issue(st);
 
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0;
-    float a0s = 0.f, a1s = 0.f, a2s = 0.f, a5s = 0.f, umax2 = 0.f;
+    float a0s = 0.f, a1s = 0.f, a2s = 0.f, a5s = 0.f, a6s = 0.f, umax2 = 0.f;
     int nbad = 0;
     for (int k = 0; k < nrows; k += S) {
 #pragma unroll
@@ -363,6 +376,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                 const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jx * jx + jy * jy + jz * jz, dr) : dr;
                 const float k45 = 4.5f * irho;
                 dst[0][kk] = fmaf(omc, f[0], ow[0] * a0);
+                float link = 0.f;  // post-collision populations that cross an interior x plane
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     if (opp<L>(i) < i) continue;
@@ -371,8 +385,15 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     const float cj = (float)L::c(i, 0) * jx + (float)L::c(i, 1) * jy + (float)L::c(i, 2) * jz;
                     const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
                     const float anti = ow3[cls] * cj;
-                    dst[i][kk] = fmaf(omc, f[i], sym + anti);
-                    dst[o][kk] = fmaf(omc, f[o], sym - anti);
+                    const float out_i = fmaf(omc, f[i], sym + anti);
+                    const float out_o = fmaf(omc, f[o], sym - anti);
+                    dst[i][kk] = out_i;
+                    dst[o][kk] = out_o;
+                    if (OBS && L::c(i, 0) != 0) {
+                        // direction i reaches fluid iff the source of o is fluid, and vice versa
+                        if ((sfq[st] >> o) & 1u) link += (float)L::c(i, 0) * out_i;
+                        if ((sfq[st] >> i) & 1u) link += (float)L::c(o, 0) * out_o;
+                    }
                 }
                 if (OBS) {
                     // Within one strip (at most 8 rows x 32 lanes) the sums are
@@ -383,7 +404,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     const float pz = (L::D == 3) ? sf[(Q + 2) * 32] : 0.f;
                     const float ex = ux - px, ey = uy - py, ez = uz - pz;
                     const float uu = ux * ux + uy * uy + uz * uz;
-                    a0s += jx;
+                    a0s += link;
+                    a6s += jx;
                     a1s += ex * ex + ey * ey + ez * ez;
                     a2s += uu;
                     umax2 = fmaxf(umax2, uu);
@@ -402,6 +424,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
         a1s = warp_sumf(a1s);
         a2s = warp_sumf(a2s);
         a5s = warp_sumf(a5s);
+        a6s = warp_sumf(a6s);
         umax2 = warp_maxf(umax2);
         nbad = __reduce_add_sync(kFull, nbad);
         v0 = a0s;
@@ -418,7 +441,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             p[3] = v3;
             p[4] = v4;
             p[5] = v5;
-            p[6] = 0.0;
+            p[6] = a6s;
             p[7] = 0.0;
         }
     }
@@ -457,10 +480,11 @@ __global__ void __launch_bounds__(256)
     const uint32_t mc = __ldg(G.seg_mask + gseg);
     const bool fluid = (mc >> lane) & 1u;
     const size_t PS = G.pstride;
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0;
     if (fluid) {
+        const SegLoc P = locate(D, gseg, lane);
         const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
-        float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, link = 0.f;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const float v = g[(size_t)i * PS + kd];
@@ -468,18 +492,30 @@ __global__ void __launch_bounds__(256)
             jx += (float)L::c(i, 0) * v;
             jy += (float)L::c(i, 1) * v;
             jz += (float)L::c(i, 2) * v;
+            if (L::c(i, 0) != 0) {
+                // does the population reach a fluid node across the x plane?
+                const int tx = P.x + L::c(i, 0);
+                int ty = P.y + L::c(i, 1), tz = P.z + L::c(i, 2);
+                if (ty < 0 || ty >= D.ny) ty = P.y;
+                if (tz < 0 || tz >= D.nz) tz = P.z;
+                if (tx >= 0 && tx < D.nx) {
+                    const uint32_t ts = D.seg_base + ((uint32_t)tz * D.ny + ty) * D.nseg + (tx >> 5);
+                    if ((__ldg(G.seg_mask + ts) >> (tx & 31)) & 1u) link += (float)L::c(i, 0) * v;
+                }
+            }
         }
         const float irho = 1.0f / (D.rho0 + dr);
         const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
         const float px = uprev[kd], py = uprev[PS + kd];
         const float pz = (L::D == 3) ? uprev[2 * PS + kd] : 0.f;
         const float ex = ux - px, ey = uy - py, ez = uz - pz;
-        v0 = (double)jx;
+        v0 = (double)link;
         v1 = (double)ex * ex + (double)ey * ey + (double)ez * ez;
         v2 = (double)ux * ux + (double)uy * uy + (double)uz * uz;
         v3 = sqrt(v2);
         v4 = isfinite(ux) && isfinite(uy) && isfinite(uz) ? 0.0 : 1.0;
         v5 = (double)dr;
+        v6 = (double)jx;
         uprev[kd] = ux;
         uprev[PS + kd] = uy;
         if (L::D == 3) uprev[2 * PS + kd] = uz;
@@ -490,6 +526,7 @@ __global__ void __launch_bounds__(256)
     v3 = warp_max(v3);
     v4 = warp_sum(v4);
     v5 = warp_sum(v5);
+    v6 = warp_sum(v6);
     if (lane == 0) {
         double* p = partials + (size_t)gseg * kNumObs;
         p[0] = v0;
@@ -498,7 +535,7 @@ __global__ void __launch_bounds__(256)
         p[3] = v3;
         p[4] = v4;
         p[5] = v5;
-        p[6] = 0.0;
+        p[6] = v6;
         p[7] = 0.0;
     }
 }
@@ -507,32 +544,29 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_reduce_obs(const DomainDev* __restrict__ dom, const double* __restrict__ partials,
                  double* __restrict__ obs, int item_mode) {
-    __shared__ double sh[kNumObs][256];
+    constexpr int K = 7;  // slots 0..6; slot 3 is a maximum, the others sums
+    __shared__ double sh[K][256];
     const int d = blockIdx.x;
     const uint32_t base = item_mode ? dom[d].item_base : dom[d].seg_base;
     const uint32_t n = item_mode ? dom[d].nitems : dom[d].nseg_dom;
-    double a[6] = {0, 0, 0, 0, 0, 0};
+    double a[K] = {0, 0, 0, 0, 0, 0, 0};
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const double* p = partials + (size_t)(base + i) * kNumObs;
-        a[0] += p[0];
-        a[1] += p[1];
-        a[2] += p[2];
-        a[3] = fmax(a[3], p[3]);
-        a[4] += p[4];
-        a[5] += p[5];
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = (k == 3) ? fmax(a[k], p[k]) : a[k] + p[k];
     }
-    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = a[k];
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = a[k];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) {
-            for (int k = 0; k < 6; ++k) {
+            for (int k = 0; k < K; ++k) {
                 const double o = sh[k][threadIdx.x + w];
                 sh[k][threadIdx.x] = (k == 3) ? fmax(sh[k][threadIdx.x], o) : sh[k][threadIdx.x] + o;
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x < kNumObs) obs[(size_t)d * kNumObs + threadIdx.x] = threadIdx.x < 6 ? sh[threadIdx.x][0] : 0.0;
+    if (threadIdx.x < kNumObs) obs[(size_t)d * kNumObs + threadIdx.x] = threadIdx.x < K ? sh[threadIdx.x][0] : 0.0;
 }
 
 // Rest equilibrium with a linear density ramp: drho(x) = drho_in (N_x-1-x)/(N_x-1).
@@ -659,6 +693,104 @@ __global__ void __launch_bounds__(256)
         g[(size_t)i * G.pstride + kd] = (float)L::wd(i) * geq;
     }
     for (int a = 0; a < L::D; ++a) uprev[(size_t)a * G.pstride + kd] = u[a];
+}
+
+// Normalised steady fields of one 2D domain, the training targets of the
+// warm-start network: out[n*3 + 0] = (rho - rho_0)/drho - (1 - x/(N_x - 1)),
+// the density's deviation from the linear inlet-to-outlet ramp; out[n*3 + 1..2]
+// = u * scale_u with scale_u = nu (N_x - 1)/(c_s^2 drho); zero on solids.  In
+// the Stokes regime these depend on the geometry (and weakly on tau) only.
+template <class L>
+__global__ void __launch_bounds__(256)
+    k_export_targets(Geometry G, uint32_t base, uint32_t nseg, double rho0, double inv_drho, double scale_u,
+                     const float* __restrict__ g, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nseg) return;
+    const uint32_t gseg = base + w;
+    const DomainDev D = G.dom[__ldg(G.seg_dom + gseg)];
+    const SegLoc P = locate(D, gseg, lane);
+    if (P.x >= D.nx) return;
+    const uint32_t mc = __ldg(G.seg_mask + gseg);
+    const size_t n = ((size_t)P.z * D.ny + P.y) * D.nx + P.x;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    if ((mc >> lane) & 1u) {
+        const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
+        double dr = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double v = (double)g[(size_t)i * G.pstride + kd];
+            dr += v;
+            jx += L::c(i, 0) * v;
+            jy += L::c(i, 1) * v;
+        }
+        const double r = rho0 + dr;
+        t0 = (float)(dr * inv_drho - (1.0 - (double)P.x / (double)(D.nx - 1)));
+        t1 = (float)(jx / r * scale_u);
+        t2 = (float)(jy / r * scale_u);
+    }
+    out[n * 3 + 0] = t0;
+    out[n * 3 + 1] = t1;
+    out[n * 3 + 2] = t2;
+}
+
+// Warm start from a normalised prediction (bf16, channel stride ld): drho =
+// drho_scale (p0 + 1 - x/(N_x - 1)), u = (p1, p2) / scale_u clipped to
+// |u| <= umax; populations = g_eq(drho, u), u_prev = u.  Solid nodes are
+// untouched (they hold nothing).
+template <class L, int EQ>
+__global__ void __launch_bounds__(256)
+    k_warm_start(Geometry G, uint32_t base, uint32_t nseg, const __nv_bfloat16* __restrict__ pred, int ld,
+                 float drho_scale, float inv_scale_u, float umax, float* __restrict__ g, float* __restrict__ uprev) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nseg) return;
+    const uint32_t gseg = base + w;
+    const uint32_t mc = __ldg(G.seg_mask + gseg);
+    if (!((mc >> lane) & 1u)) return;
+    const DomainDev D = G.dom[__ldg(G.seg_dom + gseg)];
+    const SegLoc P = locate(D, gseg, lane);
+    const size_t n = ((size_t)P.z * D.ny + P.y) * D.nx + P.x;
+    const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
+    const float ramp = 1.0f - (float)P.x / (float)(D.nx - 1);
+    const float dr = (__bfloat162float(pred[n * ld]) + ramp) * drho_scale;
+    float ux = __bfloat162float(pred[n * ld + 1]) * inv_scale_u;
+    float uy = __bfloat162float(pred[n * ld + 2]) * inv_scale_u;
+    const float um = sqrtf(ux * ux + uy * uy);
+    if (um > umax) {
+        ux *= umax / um;
+        uy *= umax / um;
+    }
+    const float rho = D.rho0 + dr;
+    const float jx = rho * ux, jy = rho * uy, jj = jx * jx + jy * jy;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const float cj = (float)L::c(i, 0) * jx + (float)L::c(i, 1) * jy;
+        float geq = dr + 3.0f * cj;
+        if (EQ == 0) geq += (4.5f * cj * cj - 1.5f * jj) / rho;
+        g[(size_t)i * G.pstride + kd] = (float)L::wd(i) * geq;
+    }
+    uprev[kd] = ux;
+    uprev[G.pstride + kd] = uy;
+}
+
+cudaError_t launch_export_targets(const Geometry& G, uint32_t base, uint32_t nseg, double rho0, double inv_drho,
+                                  double scale_u, const float* g, float* out, cudaStream_t st) {
+    const unsigned nb = (nseg + 7) / 8;
+    if (nb == 0) return cudaSuccess;
+    k_export_targets<D2Q9><<<nb, 256, 0, st>>>(G, base, nseg, rho0, inv_drho, scale_u, g, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_start(int eq, const Geometry& G, uint32_t base, uint32_t nseg, const void* pred, int ld,
+                              float drho_scale, float inv_scale_u, float umax, float* g, float* uprev,
+                              cudaStream_t st) {
+    const unsigned nb = (nseg + 7) / 8;
+    if (nb == 0) return cudaSuccess;
+    const __nv_bfloat16* p = (const __nv_bfloat16*)pred;
+    if (eq == 0) k_warm_start<D2Q9, 0><<<nb, 256, 0, st>>>(G, base, nseg, p, ld, drho_scale, inv_scale_u, umax, g, uprev);
+    else k_warm_start<D2Q9, 1><<<nb, 256, 0, st>>>(G, base, nseg, p, ld, drho_scale, inv_scale_u, umax, g, uprev);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,12 @@ cudaError_t launch_seg_setup(const DomainDev* dom, const uint32_t* dom_begin, in
                              uint32_t* seg_mask, uint32_t* seg_cnt, uint32_t* seg_off,
                              uint32_t* scan_totals, uint32_t* grand_total, cudaStream_t st);
 
+cudaError_t launch_export_targets(const Geometry& G, uint32_t base, uint32_t nseg, double rho0, double inv_drho,
+                                  double scale_u, const float* g, float* out, cudaStream_t st);
+cudaError_t launch_warm_start(int eq, const Geometry& G, uint32_t base, uint32_t nseg, const void* pred, int ld,
+                              float drho_scale, float inv_scale_u, float umax, float* g, float* uprev,
+                              cudaStream_t st);
+
 // QSGS (qsgs.cu).  keys: N uint64 scratch; counter: one uint64 scratch.
 struct QsgsScratch {
     uint64_t* keys;

@@ -55,6 +55,7 @@ class lbm_options(C.Structure):
         ("use_graphs", C.c_int32),
         ("cancel_flag", C.c_void_p),
         ("strip_rows", C.c_int32),
+        ("k_tol", C.c_double),
     ]
 
 
@@ -110,6 +111,23 @@ def load(path: Optional[str] = None):
         "lbm_set_fields": (i32, [P, i32, P, P, P, P, i32]),
         "lbm_get_step": (i32, [P, P]),
         "lbm_get_history": (i32, [P, i32, P, P, P, P, i32, P]),
+        "lbm_nn_conv_fwd": (i32, [P, i32, i32, i32, i32, P, P, i32, i32, i32, P, P, P]),
+        "lbm_nn_conv_bwd_data": (i32, [P, i32, i32, i32, i32, P, i32, i32, P, P, P]),
+        "lbm_nn_conv_bwd_weight": (i32, [P, P, i32, i32, i32, i32, i32, i32, P, P, i32, P, C.c_size_t, P]),
+        "lbm_nn_relu_bwd": (i32, [P, P, P, C.c_size_t, P]),
+        "lbm_nn_pool2_fwd": (i32, [P, i32, i32, i32, i32, P, P]),
+        "lbm_nn_pool2_bwd": (i32, [P, i32, i32, i32, i32, P, P]),
+        "lbm_nn_up2_fwd": (i32, [P, i32, i32, i32, i32, P, P]),
+        "lbm_nn_up2_bwd": (i32, [P, i32, i32, i32, i32, P, P]),
+        "lbm_nn_copy_channels": (i32, [P, i32, i32, P, i32, i32, i32, C.c_size_t, P]),
+        "lbm_nn_mse": (i32, [P, i32, P, P, C.c_size_t, i32, C.c_float, P, P, P, P]),
+        "lbm_nn_adamw": (i32, [P, P, P, P, C.c_size_t, C.c_float, C.c_float, C.c_float, C.c_float,
+                               C.c_float, i32, P, P]),
+        "lbm_nn_f32_to_bf16": (i32, [P, P, C.c_size_t, P]),
+        "lbm_nn_add": (i32, [P, P, P, C.c_size_t, P]),
+        "lbm_nn_make_input": (i32, [P, i32, i32, C.c_float, P, P]),
+        "lbm_nn_targets": (i32, [P, i32, P]),
+        "lbm_warm_start": (i32, [P, i32, P, i32]),
         "lbm_save": (i32, [P, C.c_char_p]),
         "lbm_load": (i32, [C.c_char_p, P, P]),
     }
@@ -143,9 +161,9 @@ def current_stream() -> Optional[int]:
     return None
 
 
-def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=50,
+def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=200,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
-                 use_graphs=True, cancel_flag=None, strip_rows=0) -> lbm_options:
+                 use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -158,6 +176,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.use_graphs = 1 if use_graphs else 0
     o.cancel_flag = cancel_flag
     o.strip_rows = strip_rows
+    o.k_tol = k_tol
     return o
 
 
@@ -362,6 +381,86 @@ def lbm_get_history(s: Solver, d: int = 0):
     _check(load().lbm_get_history(s.handle, d, _ptr(st), _ptr(k), _ptr(r), _ptr(t), n, C.byref(cnt)),
            s.handle)
     return st, k, r, t
+
+
+# ---------------------------------------------------------------------------
+# warm-start network kernels: device pointers (ints, or objects with
+# data_ptr(), e.g. torch CUDA tensors) in, nothing computed here
+# ---------------------------------------------------------------------------
+def _dp(t):
+    if t is None:
+        return None
+    return C.c_void_p(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))
+
+
+def lbm_nn_conv_fwd(x, n, h, w, cin, wts, bias, taps, cout, relu, out, out_f32=None, stream=None):
+    _check(load().lbm_nn_conv_fwd(_dp(x), n, h, w, cin, _dp(wts), _dp(bias), taps, cout, int(relu),
+                                  _dp(out), _dp(out_f32), stream))
+
+
+def lbm_nn_conv_bwd_data(gout, n, h, w, cout, wts, taps, cin, wflip, gin, stream=None):
+    _check(load().lbm_nn_conv_bwd_data(_dp(gout), n, h, w, cout, _dp(wts), taps, cin, _dp(wflip), _dp(gin),
+                                       stream))
+
+
+def lbm_nn_conv_bwd_weight(x, gout, n, h, w, cin, cout, taps, dw, db, accumulate, scratch, scratch_floats,
+                           stream=None):
+    _check(load().lbm_nn_conv_bwd_weight(_dp(x), _dp(gout), n, h, w, cin, cout, taps, _dp(dw), _dp(db),
+                                         int(accumulate), _dp(scratch), int(scratch_floats), stream))
+
+
+def lbm_nn_relu_bwd(y, gy, gx, count, stream=None):
+    _check(load().lbm_nn_relu_bwd(_dp(y), _dp(gy), _dp(gx), int(count), stream))
+
+
+def lbm_nn_pool2_fwd(x, n, h, w, c, out, stream=None):
+    _check(load().lbm_nn_pool2_fwd(_dp(x), n, h, w, c, _dp(out), stream))
+
+
+def lbm_nn_pool2_bwd(gout, n, h, w, c, gin, stream=None):
+    _check(load().lbm_nn_pool2_bwd(_dp(gout), n, h, w, c, _dp(gin), stream))
+
+
+def lbm_nn_up2_fwd(x, n, h, w, c, out, stream=None):
+    _check(load().lbm_nn_up2_fwd(_dp(x), n, h, w, c, _dp(out), stream))
+
+
+def lbm_nn_up2_bwd(gout, n, h, w, c, gin, stream=None):
+    _check(load().lbm_nn_up2_bwd(_dp(gout), n, h, w, c, _dp(gin), stream))
+
+
+def lbm_nn_copy_channels(src, sld, sc0, dst, dld, dc0, nc, npix, stream=None):
+    _check(load().lbm_nn_copy_channels(_dp(src), sld, sc0, _dp(dst), dld, dc0, nc, int(npix), stream))
+
+
+def lbm_nn_mse(pred, ld, target, solid, npix, nout, inv_count, grad, scratch256, loss, stream=None):
+    _check(load().lbm_nn_mse(_dp(pred), ld, _dp(target), _dp(solid), int(npix), nout, float(inv_count),
+                             _dp(grad), _dp(scratch256), _dp(loss), stream))
+
+
+def lbm_nn_adamw(p, g, m, v, n, lr, b1, b2, eps, wd, step, p_bf16=None, stream=None):
+    _check(load().lbm_nn_adamw(_dp(p), _dp(g), _dp(m), _dp(v), int(n), lr, b1, b2, eps, wd, int(step),
+                               _dp(p_bf16), stream))
+
+
+def lbm_nn_add(a, b, out, n, stream=None):
+    _check(load().lbm_nn_add(_dp(a), _dp(b), _dp(out), int(n), stream))
+
+
+def lbm_nn_f32_to_bf16(a, b, n, stream=None):
+    _check(load().lbm_nn_f32_to_bf16(_dp(a), _dp(b), int(n), stream))
+
+
+def lbm_nn_make_input(solid, h, w, tau_feat, out, stream=None):
+    _check(load().lbm_nn_make_input(_dp(solid), h, w, float(tau_feat), _dp(out), stream))
+
+
+def lbm_nn_targets(s: Solver, d: int, out) -> None:
+    _check(load().lbm_nn_targets(s.handle, d, _dp(out)), s.handle)
+
+
+def lbm_warm_start(s: Solver, d: int, pred, ld: int) -> None:
+    _check(load().lbm_warm_start(s.handle, d, _dp(pred), ld), s.handle)
 
 
 def lbm_get_step(s: Solver) -> int:

@@ -201,7 +201,8 @@ def test_observables_match_oracle_moments():
     jx = (rho * ux)[fluid].sum()
     du2 = ((ux - uxp) ** 2 + (uy - uyp) ** 2)[fluid].sum()
     u2 = (ux ** 2 + uy ** 2)[fluid].sum()
-    assert obs[0] == pytest.approx(jx, rel=1e-5)
+    assert obs[0] == pytest.approx(O.link_flux(mask, f).sum(), rel=1e-5)
+    assert obs[6] == pytest.approx(jx, rel=1e-5)
     assert obs[1] == pytest.approx(du2, rel=1e-3)
     assert obs[2] == pytest.approx(u2, rel=1e-5)
     assert obs[3] == pytest.approx(np.sqrt(ux ** 2 + uy ** 2)[fluid].max(), rel=1e-5)
