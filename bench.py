@@ -275,9 +275,12 @@ def measure_warmstart(args, lbm, sp):
     hist = WS.train(net, ds, epochs=args.ws_epochs, batch=8, lr=2e-3)
     t_train = time.perf_counter() - t0
     res = WS.evaluate(net, ev)
-    # plain: one domain at a time from the equilibrium start
+    # plain: one domain at a time from the equilibrium start, on the domains
+    # that converged in both batched runs
+    eq, wm = res["equilibrium"], res["warm"]
+    both = [d for d in range(len(ev)) if eq["per_domain"][d]["status"] == 0 and wm["per_domain"][d]["status"] == 0]
     plain_t, plain_steps = [], []
-    for d in range(len(ev)):
+    for d in both:
         s1 = lbm.lbm_create_domain(ev.masks_host[d], ev.taus[d], ev.drhos[d], lbm.make_options())
         lbm.lbm_run_to_steady(s1, 1e-9, 400_000)
         stp, kk, rr, tt = lbm.lbm_get_history(s1, 0)
@@ -285,9 +288,8 @@ def measure_warmstart(args, lbm, sp):
         plain_t.append(tk)
         plain_steps.append(int(stp[ik]))
         s1.close()
-    eq, wm = res["equilibrium"], res["warm"]
     return {
-        "shape": [ny, nx], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
+        "shape": [ny, nx], "domains_compared": len(both), "domains_not_converged": res["domains_not_converged"], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
         "unet_params": int(net.nparams), "epochs": args.ws_epochs, "loss_first_last": [hist[0], hist[-1]],
         "datagen_s": t_gen, "train_s": t_train, "tol_rel": args.ttp_tol,
         "plain_time_to_k_s": float(sum(plain_t)), "plain_steps_to_k": int(sum(plain_steps)),
@@ -295,8 +297,8 @@ def measure_warmstart(args, lbm, sp):
         "batched_warm_time_to_k_s": res["time_to_all_k_warm_s"],
         "batched_steps_to_k": res["steps_to_k_equilibrium"], "batched_warm_steps_to_k": res["steps_to_k_warm"],
         "warm_predict_s": wm["predict_s"], "k_rel_diff_warm_vs_equilibrium_max": res["k_rel_diff_max"],
-        "per_domain_steps_to_k": {"equilibrium": [p["steps_to_k"] for p in eq["per_domain"]],
-                                  "warm": [p["steps_to_k"] for p in wm["per_domain"]]},
+        "per_domain_steps_to_k": {"equilibrium": [eq["per_domain"][d]["steps_to_k"] for d in both],
+                                  "warm": [wm["per_domain"][d]["steps_to_k"] for d in both]},
     }
 
 

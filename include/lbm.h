@@ -309,12 +309,14 @@ lbm_status lbm_nn_up2_bwd(const void* gout, int32_t n, int32_t h, int32_t w, int
  * concatenation and its adjoint); sld/dld are the channel strides. */
 lbm_status lbm_nn_copy_channels(const void* src, int32_t sld, int32_t sc0, void* dst, int32_t dld, int32_t dc0,
                                 int32_t nc, size_t npix, void* stream);
-/* Masked mean squared error over fluid pixels (solid[p] == 0) and the first
- * nout channels, scaled by inv_count: *loss (device) = inv_count * sum d^2 and
- * grad = 2 d inv_count (bf16, stride ld; zero on solids and padding channels;
- * grad may be NULL).  target: FP32 [npix][nout].  scratch256: 256 floats. */
+/* Masked, channel-weighted mean squared error over fluid pixels (solid[p] ==
+ * 0) and the first nout <= 8 channels: *loss (device) = inv_count sum w_c d^2
+ * and grad = 2 w_c d inv_count (bf16, stride ld; zero on solids and padding
+ * channels; grad may be NULL).  target: FP32 [npix][nout].  weights: HOST
+ * array of nout floats (NULL = all 1).  scratch256: 256 floats. */
 lbm_status lbm_nn_mse(const void* pred, int32_t ld, const float* target, const uint8_t* solid, size_t npix,
-                      int32_t nout, float inv_count, void* grad, float* scratch256, float* loss, void* stream);
+                      int32_t nout, const float* weights, float inv_count, void* grad, float* scratch256,
+                      float* loss, void* stream);
 /* AdamW step (bias-corrected, decoupled weight decay) on FP32 parameters;
  * refreshes the bf16 copy p_bf16 when non-NULL.  step >= 1. */
 lbm_status lbm_nn_adamw(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2,

@@ -84,14 +84,16 @@ def up2_bwd(gy):
     return gy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def mse(pred, target, solid, inv_count):
-    """pred [..., >=nout], target [..., nout], solid bool [...]; returns (loss, grad)."""
+def mse(pred, target, solid, inv_count, weights=None):
+    """pred [..., >=nout], target [..., nout], solid bool [...], per-channel
+    weights (default 1); returns (loss, grad)."""
     nout = target.shape[-1]
+    wc = np.ones(nout) if weights is None else np.asarray(weights, float)
     d = pred[..., :nout] - target
     fl = (~solid)[..., None]
-    loss = float((d * d * fl).sum() * inv_count)
+    loss = float((wc * d * d * fl).sum() * inv_count)
     g = np.zeros_like(pred)
-    g[..., :nout] = 2.0 * d * fl * inv_count
+    g[..., :nout] = 2.0 * wc * d * fl * inv_count
     return loss, g
 
 

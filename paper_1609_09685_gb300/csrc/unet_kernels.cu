@@ -285,14 +285,20 @@ __global__ void k_copy_ch(const bf16* __restrict__ src, int sld, int sc0, bf16* 
     }
 }
 
-// Masked mean squared error over fluid nodes and the first nout channels:
-//   L = sum_{fluid p, c < nout} (pred - target)^2 / (nfluid nout),
-//   grad = 2 (pred - target) / (nfluid nout) on fluid nodes, 0 elsewhere
+// Channel weights of the loss (at most 8 channels), passed by value.
+struct ChanW {
+    float w[8];
+};
+
+// Masked, channel-weighted mean squared error over fluid nodes and the first
+// nout channels:
+//   L = inv_count sum_{fluid p, c < nout} w_c (pred - target)^2,
+//   grad = 2 w_c (pred - target) inv_count on fluid nodes, 0 elsewhere
 //   (grad has the prediction's channel stride; padding channels get 0).
-// Per-block partial losses; the host sums them.
+// Per-block partial losses, summed by k_sum_f32.
 __global__ void __launch_bounds__(256)
     k_mse(const bf16* __restrict__ pred, int ld, const float* __restrict__ target, const uint8_t* __restrict__ solid,
-          size_t npix, int nout, float inv_count, bf16* __restrict__ grad, float* __restrict__ part) {
+          size_t npix, int nout, float inv_count, ChanW cw, bf16* __restrict__ grad, float* __restrict__ part) {
     __shared__ float sh[256];
     float acc = 0.f;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix; p += (size_t)gridDim.x * blockDim.x) {
@@ -301,8 +307,8 @@ __global__ void __launch_bounds__(256)
             float gv = 0.f;
             if (c < nout && fl) {
                 const float d = __bfloat162float(pred[p * ld + c]) - target[p * nout + c];
-                acc += d * d;
-                gv = 2.f * d * inv_count;
+                acc += cw.w[c] * d * d;
+                gv = 2.f * cw.w[c] * d * inv_count;
             }
             if (grad) grad[p * ld + c] = __float2bfloat16(gv);
         }
@@ -497,10 +503,14 @@ lbm_status lbm_nn_copy_channels(const void* src, int32_t sld, int32_t sc0, void*
 }
 
 lbm_status lbm_nn_mse(const void* pred, int32_t ld, const float* target, const uint8_t* solid, size_t npix,
-                      int32_t nout, float inv_count, void* grad, float* scratch256, float* loss, void* stream) {
-    if (!pred || !target || !solid || !scratch256 || !loss || nout < 1 || nout > ld) return nn_fail("mse: bad arguments");
+                      int32_t nout, const float* weights, float inv_count, void* grad, float* scratch256, float* loss,
+                      void* stream) {
+    if (!pred || !target || !solid || !scratch256 || !loss || nout < 1 || nout > ld || nout > 8)
+        return nn_fail("mse: bad arguments");
+    lbmgb::nn::ChanW cw;
+    for (int c = 0; c < 8; ++c) cw.w[c] = (weights && c < nout) ? weights[c] : 1.f;
     lbmgb::nn::k_mse<<<256, 256, 0, (cudaStream_t)stream>>>((const bf16*)pred, ld, target, solid, npix, nout, inv_count,
-                                                           (bf16*)grad, scratch256);
+                                                           cw, (bf16*)grad, scratch256);
     lbm_status s = nn_launch_status();
     if (s != LBM_OK) return s;
     lbmgb::nn::k_sum_f32<<<1, 256, 0, (cudaStream_t)stream>>>(scratch256, 256, loss);

@@ -120,7 +120,7 @@ def load(path: Optional[str] = None):
         "lbm_nn_up2_fwd": (i32, [P, i32, i32, i32, i32, P, P]),
         "lbm_nn_up2_bwd": (i32, [P, i32, i32, i32, i32, P, P]),
         "lbm_nn_copy_channels": (i32, [P, i32, i32, P, i32, i32, i32, C.c_size_t, P]),
-        "lbm_nn_mse": (i32, [P, i32, P, P, C.c_size_t, i32, C.c_float, P, P, P, P]),
+        "lbm_nn_mse": (i32, [P, i32, P, P, C.c_size_t, i32, P, C.c_float, P, P, P, P]),
         "lbm_nn_adamw": (i32, [P, P, P, P, C.c_size_t, C.c_float, C.c_float, C.c_float, C.c_float,
                                C.c_float, i32, P, P]),
         "lbm_nn_f32_to_bf16": (i32, [P, P, C.c_size_t, P]),
@@ -433,8 +433,10 @@ def lbm_nn_copy_channels(src, sld, sc0, dst, dld, dc0, nc, npix, stream=None):
     _check(load().lbm_nn_copy_channels(_dp(src), sld, sc0, _dp(dst), dld, dc0, nc, int(npix), stream))
 
 
-def lbm_nn_mse(pred, ld, target, solid, npix, nout, inv_count, grad, scratch256, loss, stream=None):
-    _check(load().lbm_nn_mse(_dp(pred), ld, _dp(target), _dp(solid), int(npix), nout, float(inv_count),
+def lbm_nn_mse(pred, ld, target, solid, npix, nout, inv_count, grad, scratch256, loss, stream=None,
+               weights=None):
+    wts = None if weights is None else (C.c_float * nout)(*[float(v) for v in weights])
+    _check(load().lbm_nn_mse(_dp(pred), ld, _dp(target), _dp(solid), int(npix), nout, wts, float(inv_count),
                              _dp(grad), _dp(scratch256), _dp(loss), stream))
 
 

@@ -276,9 +276,17 @@ def generate(domains, shape, stream=None, max_steps: int = 400_000, tol: float =
     return ds
 
 
+# Loss weights of (density deviation, u_x, u_y).  The density deviation from
+# the ramp is ~5x smaller than the normalised velocity but it is what sets the
+# slow pressure-diffusion mode the iteration has to relax; the velocity
+# relaxes to the local pressure gradient on the fast pore-viscous time scale.
+LOSS_WEIGHTS = (25.0, 1.0, 1.0)
+
+
 def train(net: UNet, ds: Dataset, epochs: int = 20, batch: int = 8, lr: float = 2e-3, seed: int = 0,
-          log=None):
-    """AdamW on the masked MSE of the normalised fields; returns per-epoch mean losses."""
+          log=None, weights=LOSS_WEIGHTS):
+    """AdamW on the masked, channel-weighted MSE of the normalised fields;
+    returns per-epoch mean losses."""
     torch = _torch()
     s = net.ctx.stream
     n = len(ds)
@@ -299,7 +307,8 @@ def train(net: UNet, ds: Dataset, epochs: int = 20, batch: int = 8, lr: float = 
             y = net.forward(x, batch, ds.h, ds.w)
             nfl = sum(nfluid[i0:i0 + batch])
             lbm.lbm_nn_mse(y, C_OUT, ds.targets[i0:i0 + batch], ds.solid[i0:i0 + batch],
-                           batch * ds.h * ds.w, N_TARGET, 1.0 / (N_TARGET * nfl), grad, part, lossd, s)
+                           batch * ds.h * ds.w, N_TARGET, 1.0 / (N_TARGET * nfl), grad, part, lossd, s,
+                           weights=weights)
             net.backward(grad, batch)
             # cosine learning-rate decay
             frac = net.t / max(total_steps, 1)
@@ -356,9 +365,16 @@ def evaluate(net: UNet, ds: Dataset, stream=None, tol_k: float = 1e-4, max_steps
         s.close()
         res[mode] = {"k": [float(v) for v in k], "per_domain": per, "wall_s": t_run, "predict_s": t_pred}
     eq, wm = res["equilibrium"], res["warm"]
-    res["k_rel_diff_max"] = float(np.max(np.abs(np.array(wm["k"]) - np.array(eq["k"])) / np.abs(eq["k"])))
-    res["steps_to_k_equilibrium"] = int(np.sum([p["steps_to_k"] for p in eq["per_domain"]]))
-    res["steps_to_k_warm"] = int(np.sum([p["steps_to_k"] for p in wm["per_domain"]]))
-    res["time_to_all_k_equilibrium_s"] = max(p["time_to_k"] for p in eq["per_domain"])
-    res["time_to_all_k_warm_s"] = max(p["time_to_k"] for p in wm["per_domain"])
+    # compare on the domains that converged in both runs (a domain with almost
+    # no through-path can need more than max_steps from any start)
+    both = [d for d in range(n) if eq["per_domain"][d]["status"] == 0 and wm["per_domain"][d]["status"] == 0]
+    res["domains_converged_both"] = len(both)
+    res["domains_not_converged"] = n - len(both)
+    keq = np.array([eq["k"][d] for d in both])
+    kwm = np.array([wm["k"][d] for d in both])
+    res["k_rel_diff_max"] = float(np.max(np.abs(kwm - keq) / np.abs(keq))) if both else None
+    res["steps_to_k_equilibrium"] = int(np.sum([eq["per_domain"][d]["steps_to_k"] for d in both]))
+    res["steps_to_k_warm"] = int(np.sum([wm["per_domain"][d]["steps_to_k"] for d in both]))
+    res["time_to_all_k_equilibrium_s"] = max([eq["per_domain"][d]["time_to_k"] for d in both], default=None)
+    res["time_to_all_k_warm_s"] = max([wm["per_domain"][d]["time_to_k"] for d in both], default=None)
     return res

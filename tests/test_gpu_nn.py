@@ -110,8 +110,8 @@ def test_mse_adamw_input():
     part = torch.empty(256, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
     lbm.lbm_nn_mse(predt, 16, torch.tensor(tgt, device="cuda"), torch.tensor(solid, device="cuda"), npix, 3,
-                   inv, grad, part, loss)
-    lref, gref = R.mse(pred, tgt.astype(np.float64), solid.astype(bool), inv)
+                   inv, grad, part, loss, weights=[4.0, 1.0, 0.5])
+    lref, gref = R.mse(pred, tgt.astype(np.float64), solid.astype(bool), inv, weights=[4.0, 1.0, 0.5])
     assert float(loss.item()) == pytest.approx(lref, rel=1e-5)
     _close(_np(grad), gref, 1e-2)
     p = rng.standard_normal(1000).astype(np.float32)
