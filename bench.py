@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
-    p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "small"], default="sweep")
+    p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="sweep")
     p.add_argument("--interval", type=int, default=100)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -69,11 +69,27 @@ def get_workload(name: str, rank: int) -> workloads.Workload:
         return workloads.batch128(master_seed=2026 + rank)
     if name == "d3q19":
         return workloads.d3q19_256(seed=1 + rank)
+    if name == "d3q19_one":
+        return workloads.d3q19_256(taus=(0.6,), seed=1 + rank)
     return workloads.small_2d(seed=1 + rank)
 
 
 def lattice_q(wl):
     return 19 if wl.domains[0].nz > 1 else 9
+
+
+def combine_ranks(dist, device, maxima, sums):
+    """Whole-job figures of a weak-scaling run: each rank solves its own
+    independent domains (no data-path collective); timing takes the slowest
+    rank (MAX) and work adds up over ranks (SUM).  Returns (maxima, sums)."""
+    if dist is None:
+        return list(maxima), list(sums)
+    import torch
+    a = torch.tensor(list(maxima), dtype=torch.float64, device=device)
+    b = torch.tensor(list(sums), dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
 
 
 # ---------------------------------------------------------------------------
@@ -398,13 +414,7 @@ def run_native(args):
         clocks = sampler.stop()
     t = e0.elapsed_time(e1) / 1e3
     t_kern = sum(a.elapsed_time(b) for a, b in zip(ka, kb)) / 1e3 / (args.steps * (N - 1))
-    updates = float(args.steps * N * fluid)
-    if dist is not None:
-        tt = torch.tensor([t, t_kern], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        uu = torch.tensor([updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(uu)
-        t, t_kern, updates = float(tt[0]), float(tt[1]), float(uu[0])
+    (t, t_kern), (updates,) = combine_ranks(dist, "cuda", [t, t_kern], [float(args.steps * N * fluid)])
     value = updates / t / 1e6
 
     # end to end through the C ABI: host masks (pinned) -> create -> one interval
@@ -427,13 +437,7 @@ def run_native(args):
         s2.close()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    e2e_updates = float(args.e2e_steps * N * fluid)
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        uu = torch.tensor([e2e_updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(uu)
-        t_e2e, e2e_updates = float(tt[0]), float(uu[0])
+    (t_e2e,), (e2e_updates,) = combine_ranks(dist, "cuda", [t_e2e], [float(args.e2e_steps * N * fluid)])
     s.close()
     ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
     ws = measure_warmstart(args, lbm, sp) if (args.warmstart and rank == 0) else None

@@ -67,7 +67,7 @@ typedef struct lbm_options {
     double stall_floor;      /* stall rule applies only while r < stall_floor (default 1e-5) */
     double rho_out;          /* outlet density rho_0 (default 1.0) */
     void* stream;            /* cudaStream_t; NULL = legacy default stream */
-    int32_t block_threads;   /* stream-collide block size, a multiple of 32 up to 256; 0 = 256 */
+    int32_t block_threads;   /* stream-collide block size, a multiple of 32 up to 256; 0 = 128 */
     int32_t use_graphs;      /* capture each check interval as a CUDA graph (default 1) */
     volatile const int32_t* cancel_flag; /* host flag polled between intervals; nonzero cancels */
     int32_t strip_rows;      /* rows per stream-collide work item (0 = default 8, max 255) */

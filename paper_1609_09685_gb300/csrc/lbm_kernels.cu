@@ -150,20 +150,22 @@ struct Dir {
     static constexpr int row = (1 - cy) + (L::NROW == 9 ? 3 * (1 - cz) : 0);
 };
 
-// Source of direction I for the node of window set w (pull streaming): the
-// fluid source's compact slot in the (possibly mirrored) direction plane, or
-// the node's own opposite slot when the source is solid (bounce-back).
+// Source element of direction I for the node of window set w (pull
+// streaming): the fluid source's compact slot in the (possibly mirrored)
+// direction plane, or the node's own opposite slot when the source is solid
+// (bounce-back).  Plane offsets are compile-time multiples of the uniform
+// plane stride, so they stay in uniform registers.
 template <class L, int I>
-__device__ __forceinline__ const float* src_ptr(const HotArgs& A, const Win (&w)[L::NROW], uint32_t kd, bool my,
-                                                bool mz) {
+__device__ __forceinline__ uint32_t src_elem(const Win (&w)[L::NROW], uint32_t PS, uint32_t kd, bool my, bool mz) {
     using d = Dir<I, L>;
     const Win& wn = w[d::row];
     const bool sf = win_fluid<d::cx>(wn);
-    const float* plane = A.src[I];
-    if (d::cy != 0 && d::cz != 0) plane = my ? (mz ? A.src[d::fyz] : A.src[d::fy]) : (mz ? A.src[d::fz] : A.src[I]);
-    else if (d::cy != 0) plane = my ? A.src[d::fy] : A.src[I];
-    else if (d::cz != 0) plane = mz ? A.src[d::fz] : A.src[I];
-    return sf ? plane + win_idx<d::cx>(wn) : A.src[d::o] + kd;
+    uint32_t plane = (uint32_t)I * PS;
+    if (d::cy != 0 && d::cz != 0)
+        plane = my ? (mz ? (uint32_t)d::fyz * PS : (uint32_t)d::fy * PS) : (mz ? (uint32_t)d::fz * PS : plane);
+    else if (d::cy != 0) plane = my ? (uint32_t)d::fy * PS : plane;
+    else if (d::cz != 0) plane = mz ? (uint32_t)d::fz * PS : plane;
+    return sf ? plane + win_idx<d::cx>(wn) : (uint32_t)d::o * PS + kd;
 }
 
 // Bit i set when the pull source of direction i is fluid.  The destination of
@@ -188,12 +190,12 @@ __device__ __forceinline__ void cp_async_wait() {
 // slot of the next fluid node (at most the padding slot nfluid < pstride), so
 // every address is in bounds; the value is discarded.
 template <class L, int... Is>
-__device__ __forceinline__ void issue_row(const HotArgs& A, const Win (&w)[L::NROW], uint32_t kd, bool ylo,
-                                          bool yhi, bool zlo, bool zhi, uint32_t sbase,
+__device__ __forceinline__ void issue_row(const float* __restrict__ src, uint32_t PS, const Win (&w)[L::NROW],
+                                          uint32_t kd, bool ylo, bool yhi, bool zlo, bool zhi, uint32_t sbase,
                                           std::integer_sequence<int, Is...>) {
     // a direction with c_y = +1 pulls from row y - 1, mirrored when y = 0, etc.
     (cp_async4(sbase + 4u * (32u * Is),
-               src_ptr<L, Is>(A, w, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, Dir<Is, L>::cz > 0 ? zlo : zhi)),
+               src + src_elem<L, Is>(w, PS, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, Dir<Is, L>::cz > 0 ? zlo : zhi)),
      ...);
 }
 
@@ -212,10 +214,17 @@ struct MinBlocks {
     static constexpr int value = (L::Q == 9) ? LBM_SC_MINB_2D : LBM_SC_MINB_3D;
 };
 
-#ifndef LBM_SC_STAGES
-#define LBM_SC_STAGES 3  // rows in flight per warp in the cp.async pipeline
+// Rows in flight per warp in the cp.async pipeline (D2Q9 / D3Q19).
+#ifndef LBM_SC_STAGES_2D
+#define LBM_SC_STAGES_2D 3
 #endif
-constexpr int kStages = LBM_SC_STAGES;
+#ifndef LBM_SC_STAGES_3D
+#define LBM_SC_STAGES_3D 3
+#endif
+template <class L>
+__host__ __device__ constexpr int stages() {
+    return L::Q == 9 ? LBM_SC_STAGES_2D : LBM_SC_STAGES_3D;
+}
 
 // Shared-memory slots per stage: the Q source populations, plus the D
 // components of u_prev when the step also observes.
@@ -225,7 +234,7 @@ __host__ __device__ constexpr int stage_slots() {
 }
 template <class L, bool OBS>
 constexpr size_t sc_smem_bytes(int threads) {
-    return (size_t)(threads / 32) * kStages * stage_slots<L, OBS>() * 32 * sizeof(float);
+    return (size_t)(threads / 32) * stages<L>() * stage_slots<L, OBS>() * 32 * sizeof(float);
 }
 
 // A warp walks its strip row by row.  Rows k+1 .. k+S-1 are already in
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     k_stream_collide(const __grid_constant__ HotArgs A, float* __restrict__ uprev, double* __restrict__ partials) {
     constexpr int Q = L::Q;
     constexpr int NZ = (L::NROW == 9) ? 3 : 1;
-    constexpr int S = kStages;
+    constexpr int S = stages<L>();
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -262,7 +271,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     const float om = D.omega, omc = 1.0f - D.omega;
     const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
     const float ow3[3] = {3.0f * ow[0], 3.0f * ow[1], 3.0f * ow[2]};
-    float* const* dst = A.dst;
+    float* const dst0 = A.dst[0];  // plane i starts at dst0 + i * PS
     constexpr int SL = stage_slots<L, OBS>();
     float* wbuf = smem + (size_t)wid * S * SL * 32;
     const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(wbuf) + 4u * lane;
@@ -278,16 +287,21 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
         pbase[zi] = (uint32_t)zz * (uint32_t)ny;
     }
     auto rowc = [&](int yy) { return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy); };
-    // windows of rows r-1, r, r+1 for the next row r to issue, and the raw
-    // record of row r+2 loaded one issue ahead
-    Win wm[NZ], wc[NZ], wp[NZ];
-    uint4 rn[NZ];
+    // D2Q9 slides the windows of rows r-1, r, r+1 down the strip (one new
+    // record per row, prefetched one issue ahead); D3Q19 would need 9 sliding
+    // windows, so it reloads its 9 records per row from L1 instead.
+    constexpr bool kSlide = (NZ == 1);
+    constexpr int NW = kSlide ? NZ : 1;
+    Win wm[NW], wc[NW], wp[NW];
+    uint4 rn[NW];
+    if (kSlide) {
 #pragma unroll
-    for (int zi = 0; zi < NZ; ++zi) {
-        wm[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 - 1)) * rs), lane, lmask);
-        wc[zi] = make_win(__ldg(wcol + (pbase[zi] + y0) * rs), lane, lmask);
-        wp[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 + 1)) * rs), lane, lmask);
-        rn[zi] = __ldg(wcol + (pbase[zi] + rowc(y0 + 2)) * rs);
+        for (int zi = 0; zi < NW; ++zi) {
+            wm[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 - 1)) * rs), lane, lmask);
+            wc[zi] = make_win(__ldg(wcol + (pbase[zi] + y0) * rs), lane, lmask);
+            wp[zi] = make_win(__ldg(wcol + (pbase[zi] + rowc(y0 + 1)) * rs), lane, lmask);
+            rn[zi] = __ldg(wcol + (pbase[zi] + rowc(y0 + 2)) * rs);
+        }
     }
     int next = 0;  // next row (relative to y0) to issue
     bool flq[S];
@@ -298,24 +312,33 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
         if (next < nrows) {
             const int y = y0 + next;
             Win w[L::NROW];
+            if (kSlide) {
 #pragma unroll
-            for (int r = 0; r < L::NROW; ++r) {
-                const int zi = (NZ == 3) ? r / 3 : 0, dy = r % 3;
-                w[r] = dy == 0 ? wm[zi] : (dy == 1 ? wc[zi] : wp[zi]);
+                for (int r = 0; r < L::NROW; ++r) {
+                    const int dy = r % 3;
+                    w[r] = dy == 0 ? wm[0] : (dy == 1 ? wc[0] : wp[0]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < L::NROW; ++r) {
+                    const int zi = r / 3, dy = r % 3 - 1;
+                    w[r] = make_win(__ldg(wcol + (pbase[zi] + rowc(y + dy)) * rs), lane, lmask);
+                }
             }
             constexpr int C = (L::NROW == 9) ? 4 : 1;
             flq[st] = win_fluid<0>(w[C]);
             kdq[st] = win_idx<0>(w[C]);
             sfq[st] = OBS ? src_fluid_mask<L>(w, std::make_integer_sequence<int, Q>{}) : 0u;
             const uint32_t sbase = sb0 + 4u * (uint32_t)(st * SL * 32);
-            issue_row<L>(A, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase, std::make_integer_sequence<int, Q>{});
+            issue_row<L>(A.src[0], PS, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase,
+                         std::make_integer_sequence<int, Q>{});
             if (OBS) {
 #pragma unroll
                 for (int a = 0; a < L::D; ++a) cp_async4(sbase + 4u * (32u * (Q + a)), uprev + (size_t)a * PS + kdq[st]);
             }
-            if (next + 1 < nrows) {
+            if (kSlide && next + 1 < nrows) {
 #pragma unroll
-                for (int zi = 0; zi < NZ; ++zi) {
+                for (int zi = 0; zi < NW; ++zi) {
                     wm[zi] = wc[zi];
                     wc[zi] = wp[zi];
                     wp[zi] = make_win(rn[zi], lane, lmask);
@@ -375,7 +398,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                 // a0 = drho - 1.5 |j|^2 / rho (quadratic) or drho (linear).
                 const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jx * jx + jy * jy + jz * jz, dr) : dr;
                 const float k45 = 4.5f * irho;
-                dst[0][kk] = fmaf(omc, f[0], ow[0] * a0);
+                float* const dk = dst0 + kk;
+                dk[0] = fmaf(omc, f[0], ow[0] * a0);
                 float link = 0.f;  // post-collision populations that cross an interior x plane
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
@@ -387,8 +411,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     const float anti = ow3[cls] * cj;
                     const float out_i = fmaf(omc, f[i], sym + anti);
                     const float out_o = fmaf(omc, f[o], sym - anti);
-                    dst[i][kk] = out_i;
-                    dst[o][kk] = out_o;
+                    dk[(uint32_t)i * PS] = out_i;
+                    dk[(uint32_t)o * PS] = out_o;
                     if (OBS && L::c(i, 0) != 0) {
                         // direction i reaches fluid iff the source of o is fluid, and vice versa
                         if ((sfq[st] >> o) & 1u) link += (float)L::c(i, 0) * out_i;
@@ -918,6 +942,8 @@ static cudaError_t sc_launch(unsigned nb, int threads, const HotArgs& A, float* 
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sc_smem_bytes<L, OBS>(256));
         if (e != cudaSuccess) return e;
+        // (no carveout preference: the default keeps a large L1, which the
+        // cp.async loads need for the sectors neighbouring segments share)
         attr_set = true;
     }
     k_stream_collide<L, EQ, OBS><<<nb, threads, sm, st>>>(A, uprev, partials);
@@ -939,7 +965,7 @@ static cudaError_t sc_dispatch(int eq, bool obs, const HotArgs& A, float* uprev,
 
 cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const float* src, float* dst,
                                   float* uprev, double* partials, int threads, cudaStream_t st) {
-    if (threads <= 0) threads = 256;
+    if (threads <= 0) threads = 128;  // measured best on GB300 for both lattices
     for (int i = 0; i < 19; ++i) {
         A.src[i] = i < q ? src + (size_t)i * A.pstride : nullptr;
         A.dst[i] = i < q ? dst + (size_t)i * A.pstride : nullptr;
