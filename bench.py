@@ -313,6 +313,7 @@ def measure_warmstart(args, lbm, sp):
         "batched_warm_time_to_k_s": res["time_to_all_k_warm_s"],
         "batched_steps_to_k": res["steps_to_k_equilibrium"], "batched_warm_steps_to_k": res["steps_to_k_warm"],
         "warm_predict_s": wm["predict_s"], "k_rel_diff_warm_vs_equilibrium_max": res["k_rel_diff_max"],
+        "k_rel_diff_warm_vs_equilibrium": res["k_rel_diff"],
         "per_domain_steps_to_k": {"equilibrium": [eq["per_domain"][d]["steps_to_k"] for d in both],
                                   "warm": [wm["per_domain"][d]["steps_to_k"] for d in both]},
     }

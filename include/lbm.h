@@ -190,10 +190,11 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs);
  * is formed per domain; a domain with r < tol is converged and retired from
  * further stepping.  A domain is also converged (LBM_OK) when its permeability
  * k(t), from the FP64 mass flow rate of each check, has settled: over windows
- * of 5 checks, with D1 and D0 the last two changes of k and q = |D1/D0|, the
+ * of 10 checks, with D1 and D0 the last two changes of k and q = |D1/D0|, the
  * remaining error of a geometric approach is at most |D1| q/(1 - q); the
- * domain stops once that bound is below opt.k_tol |k| at 5 consecutive checks,
- * or once k has stayed within 0.05 opt.k_tol |k| over 40 checks (|k| is taken
+ * domain stops once that bound is below opt.k_tol |k| at 10 consecutive checks
+ * with r < 10 opt.k_tol, or once k has stayed within 0.05 opt.k_tol |k| over 40
+ * checks (|k| is taken
  * as at least 1e-3 of its largest value in the run, so that a domain whose
  * flow dies out, having no through-path, stops too).  This is the
  * stop that matters in FP32: in the Stokes regime the per-node residual

@@ -240,25 +240,28 @@ void store_obs(lbm_handle h) {
 
 // Copy a retired domain's populations into the other buffer so both hold its
 // final state (no kernel writes a retired domain).
-// Permeability-based stop.  The domain-summed FP64 flux averages out most of
-// the FP32 rounding that makes the per-node residual jitter, so k(t) converges
-// smoothly until a small jitter floor.  Over windows of W = 5 checks, the
-// changes D1 = k_i - k_(i-W) and D0 = k_(i-W) - k_(i-2W) of a geometric approach
-// shrink by q = |D1 / D0| per window and the remaining error is at most
-// |D1| q / (1 - q).  The domain stops once that bound is below k_tol |k| at 5
-// consecutive checks, or once k has stayed within 0.05 k_tol |k| over the last
-// 40 checks (the jitter floor, where the ratio carries no information).  The
-// scale of the tolerance is |k|, but at least 1e-3 of the largest |k| of the run,
-// so that a domain whose flow dies out (no through-path) also stops.
-bool k_converged(DomainHost& D, double k, double k_tol) {
+// Permeability-based stop.  The domain-summed FP64 mass flow rate averages out
+// most of the FP32 rounding that makes the per-node residual jitter, so k(t)
+// converges smoothly until a small jitter floor.  Over windows of W = 10
+// checks, the changes D1 = k_i - k_(i-W) and D0 = k_(i-W) - k_(i-2W) of a
+// geometric approach shrink by q = |D1 / D0| per window and the remaining error
+// is at most |D1| q / (1 - q).  The domain stops once that bound is below
+// k_tol |k| at 10 consecutive checks while the velocity residual r is below
+// 10 k_tol (early on, a fast mode can set q and hide a slow one; the residual
+// still sees the slow mode), or once k has stayed within 0.05 k_tol |k| over
+// the last 40 checks (the jitter floor, where the ratio carries no
+// information).  The scale of the tolerance is |k|, but at least 1e-3 of the
+// largest |k| of the run, so that a domain whose flow dies out also stops.
+bool k_converged(DomainHost& D, double k, double r, double k_tol) {
+    constexpr size_t W = 10, KEEP = 41;
     D.kq.push_back(k);
-    if (D.kq.size() > 41) D.kq.erase(D.kq.begin());
+    if (D.kq.size() > KEEP) D.kq.erase(D.kq.begin());
     const size_t n = D.kq.size();
     D.k_peak = std::max(D.k_peak, std::fabs(k));
     const double tolk = k_tol * std::max(std::fabs(k), 1e-3 * D.k_peak);
     bool ok = false;
-    if (n >= 11) {
-        const double d1 = D.kq[n - 1] - D.kq[n - 6], d0 = D.kq[n - 6] - D.kq[n - 11];
+    if (n >= 2 * W + 1 && r < 10.0 * k_tol) {
+        const double d1 = D.kq[n - 1] - D.kq[n - 1 - W], d0 = D.kq[n - 1 - W] - D.kq[n - 1 - 2 * W];
         if (d0 != 0.0) {
             const double q = std::fabs(d1 / d0);
             if (q < 1.0) ok = std::fabs(d1) * q / (1.0 - q) < tolk;
@@ -267,8 +270,8 @@ bool k_converged(DomainHost& D, double k, double k_tol) {
         }
     }
     D.k_ok = ok ? D.k_ok + 1 : 0;
-    if (D.k_ok >= 5) return true;
-    if (n == 41) {
+    if (D.k_ok >= 10) return true;
+    if (n == KEEP) {
         double lo = D.kq[0], hi = D.kq[0];
         for (double v : D.kq) {
             lo = std::min(lo, v);
@@ -679,7 +682,7 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
             const double kt = D.h_k.back();
             if (o[4] > 0.0 || !std::isfinite(o[0])) ds = LBM_DIVERGED;
             else if (r < tol) ds = LBM_OK;
-            else if (h->opt.k_tol > 0.0 && std::isfinite(kt) && k_converged(D, kt, h->opt.k_tol)) ds = LBM_OK;
+            else if (h->opt.k_tol > 0.0 && std::isfinite(kt) && k_converged(D, kt, r, h->opt.k_tol)) ds = LBM_OK;
             else {
                 // FP32 floor: below stall_floor the residual jitters instead of
                 // decaying, so it stops setting new minima; a slow but genuine

@@ -141,6 +141,39 @@ template <int CX>
 __device__ __forceinline__ bool win_fluid(const Win& w) {
     return (w.tri >> (1 - CX)) & 1u;
 }
+// c_i . v using only the non-zero components of c_i (without fast-math the
+// compiler must keep 0 * v, which is not 0 for a non-finite v).
+template <class L>
+__device__ __forceinline__ float cdot(int i, float vx, float vy, float vz) {
+    float r = 0.f;
+    if (L::c(i, 0) > 0) r += vx;
+    if (L::c(i, 0) < 0) r -= vx;
+    if (L::c(i, 1) > 0) r += vy;
+    if (L::c(i, 1) < 0) r -= vy;
+    if (L::c(i, 2) > 0) r += vz;
+    if (L::c(i, 2) < 0) r -= vz;
+    return r;
+}
+// first moments: density deviation and the momentum components, from the
+// non-zero velocity components only
+template <class L>
+__device__ __forceinline__ void moments(const float (&f)[L::Q], float& dr, float& jx, float& jy, float& jz) {
+    dr = 0.f;
+    jx = 0.f;
+    jy = 0.f;
+    jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        dr += f[i];
+        if (L::c(i, 0) > 0) jx += f[i];
+        if (L::c(i, 0) < 0) jx -= f[i];
+        if (L::c(i, 1) > 0) jy += f[i];
+        if (L::c(i, 1) < 0) jy -= f[i];
+        if (L::c(i, 2) > 0) jz += f[i];
+        if (L::c(i, 2) < 0) jz -= f[i];
+    }
+}
+
 template <int I, class L>
 struct Dir {
     static constexpr int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
@@ -384,19 +417,14 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
 #pragma unroll
                 for (int i = 0; i < Q; ++i) f[i] = xout ? g[i] : f[i];
             }
-            float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                dr += f[i];
-                jx += (float)L::c(i, 0) * f[i];
-                jy += (float)L::c(i, 1) * f[i];
-                jz += (float)L::c(i, 2) * f[i];
-            }
+            float dr, jx, jy, jz;
+            moments<L>(f, dr, jx, jy, jz);
             const float irho = __fdividef(1.0f, D.rho0 + dr);
             if (fl) {
                 // BGK by opposite pairs: f* = (1 - omega) f + omega w (a0 + 4.5 (c.j)^2/rho +- 3 c.j),
                 // a0 = drho - 1.5 |j|^2 / rho (quadratic) or drho (linear).
-                const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jx * jx + jy * jy + jz * jz, dr) : dr;
+                const float jj = (L::D == 3) ? jx * jx + jy * jy + jz * jz : jx * jx + jy * jy;
+                const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jj, dr) : dr;
                 const float k45 = 4.5f * irho;
                 float* const dk = dst0 + kk;
                 dk[0] = fmaf(omc, f[0], ow[0] * a0);
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     if (opp<L>(i) < i) continue;
                     const int o = opp<L>(i);
                     const int cls = (L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
-                    const float cj = (float)L::c(i, 0) * jx + (float)L::c(i, 1) * jy + (float)L::c(i, 2) * jz;
+                    const float cj = cdot<L>(i, jx, jy, jz);
                     const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
                     const float anti = ow3[cls] * cj;
                     const float out_i = fmaf(omc, f[i], sym + anti);
@@ -423,17 +451,17 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     // Within one strip (at most 8 rows x 32 lanes) the sums are
                     // FP32 -- the FP64 rate of this part is low -- and each
                     // strip hands one FP64 partial to the cross-strip FP64 pass.
-                    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+                    const float ux = jx * irho, uy = jy * irho, uz = (L::D == 3) ? jz * irho : 0.f;
                     const float px = sf[Q * 32], py = sf[(Q + 1) * 32];
                     const float pz = (L::D == 3) ? sf[(Q + 2) * 32] : 0.f;
                     const float ex = ux - px, ey = uy - py, ez = uz - pz;
-                    const float uu = ux * ux + uy * uy + uz * uz;
+                    const float uu = (L::D == 3) ? ux * ux + uy * uy + uz * uz : ux * ux + uy * uy;
                     a0s += link;
                     a6s += jx;
-                    a1s += ex * ex + ey * ey + ez * ez;
+                    a1s += (L::D == 3) ? ex * ex + ey * ey + ez * ez : ex * ex + ey * ey;
                     a2s += uu;
                     umax2 = fmaxf(umax2, uu);
-                    nbad += (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? 0 : 1;
+                    nbad += (isfinite(ux) && isfinite(uy) && isfinite(uz)) ? 0 : 1;  // uz = 0 in 2D
                     a5s += dr;
                     uprev[kk] = ux;
                     uprev[PS + kk] = uy;

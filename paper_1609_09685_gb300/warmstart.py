@@ -373,6 +373,7 @@ def evaluate(net: UNet, ds: Dataset, stream=None, tol_k: float = 1e-4, max_steps
     keq = np.array([eq["k"][d] for d in both])
     kwm = np.array([wm["k"][d] for d in both])
     res["k_rel_diff_max"] = float(np.max(np.abs(kwm - keq) / np.abs(keq))) if both else None
+    res["k_rel_diff"] = [float(v) for v in (kwm - keq) / np.abs(keq)] if both else []
     res["steps_to_k_equilibrium"] = int(np.sum([eq["per_domain"][d]["steps_to_k"] for d in both]))
     res["steps_to_k_warm"] = int(np.sum([wm["per_domain"][d]["steps_to_k"] for d in both]))
     res["time_to_all_k_equilibrium_s"] = max([eq["per_domain"][d]["time_to_k"] for d in both], default=None)

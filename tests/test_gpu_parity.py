@@ -277,3 +277,18 @@ def test_divergence_is_reported():
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_run_to_steady(s, 1e-9, 1000)
         assert e.value.status == lbm.LBM_DIVERGED
+
+
+def test_cancel_flag_stops_the_run_between_intervals():
+    import ctypes as C
+    mask, _ = O.qsgs((20, 40), 3, 0.02, 0.75)
+    flag = C.c_int32(1)
+    opts = lbm.make_options(cancel_flag=C.addressof(flag))
+    with lbm.lbm_create_domain(mask, 0.8, 1e-3, opts) as s:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_run_to_steady(s, 1e-9, 100000)
+        assert e.value.status == lbm.LBM_CANCELLED
+        assert lbm.lbm_get_step(s) == 0  # cancelled before the first interval
+        flag.value = 0
+        rc, st, steps, _ = lbm.lbm_run_to_steady(s, 1e-9, 100000)
+        assert st[0] == lbm.LBM_OK
