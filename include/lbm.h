@@ -72,6 +72,9 @@ typedef struct lbm_options {
     volatile const int32_t* cancel_flag; /* host flag polled between intervals; nonzero cancels */
     int32_t strip_rows;      /* rows per stream-collide work item (0 = default 8, max 255) */
     double k_tol;            /* permeability-based stop (see lbm_run_to_steady); 0 disables (default 1e-5) */
+    int32_t in_place_pairs;  /* 1 (default): advance plain steps two at a time in place (a gather step that
+                                writes each result back to the slot it read, then a step on each node's own
+                                slots); same arithmetic as two pull steps.  0: one pull step at a time. */
 } lbm_options;
 
 /* One domain of a batch. */

@@ -82,6 +82,9 @@ struct lbm_solver {
     uint32_t* d_scan = nullptr;
     uint4* d_win = nullptr;
     uint4* d_items = nullptr;
+    uint2* d_vitems = nullptr;  // local-step work items
+    uint32_t nvitems = 0;
+    uint32_t* d_face = nullptr;  // inlet/outlet bits per compact slot
     uint32_t nitems = 0;
     uint8_t* d_mask = nullptr;
     uint32_t nseg_total = 0;
@@ -113,6 +116,9 @@ struct lbm_solver {
         A.items = d_items;
         A.nitems = nitems;
         A.pstride = (uint32_t)pstride;
+        A.vitems = d_vitems;
+        A.nvitems = nvitems;
+        A.face = d_face;
         return A;
     }
 };
@@ -150,6 +156,8 @@ void free_solver(lbm_handle h) {
     cudaFree(h->d_scan);
     cudaFree(h->d_win);
     cudaFree(h->d_items);
+    cudaFree(h->d_vitems);
+    cudaFree(h->d_face);
     cudaFree(h->d_mask);
     cudaFree(h->d_g[0]);
     cudaFree(h->d_g[1]);
@@ -181,14 +189,30 @@ lbm_status upload_dom(lbm_handle h) {
     return LBM_OK;
 }
 
+// Pull steps (buffer swaps) among n steps: the observing step, and with
+// in-place pairs only an odd plain step left over.
+int64_t pull_steps(lbm_handle h, int64_t n, bool obs) {
+    const int64_t o = (obs && n > 0) ? 1 : 0;
+    const int64_t plain = n - o;
+    return o + (h->opt.in_place_pairs ? (plain & 1) : plain);
+}
+
 // Enqueue n steps (the last one observing when obs) plus the reduction and the
-// copy of the observables to pinned host memory.  Advances h->cur.
+// copy of the observables to pinned host memory.  Plain steps run as in-place
+// pairs on the current buffer (when enabled); the remaining steps pull from
+// the current buffer into the other one.  Advances h->cur.
 lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs) {
     const Geometry G = h->geom();
     const HotArgs A = h->hot();
-    for (int64_t k = 0; k < n; ++k) {
-        const bool o = obs && (k == n - 1);
-        CK(h, launch_stream_collide(h->q, h->eq, o, A, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
+    const int64_t o = (obs && n > 0) ? 1 : 0;
+    int64_t plain = n - o;
+    if (h->opt.in_place_pairs) {
+        for (; plain >= 2; plain -= 2)
+            CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+    }
+    for (int64_t k = 0; k < plain + o; ++k) {
+        const bool ob = (o == 1) && (k == plain);
+        CK(h, launch_stream_collide(h->q, h->eq, ob, A, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
                                     h->d_partials, h->opt.block_threads, h->st));
         h->cur ^= 1;
     }
@@ -226,7 +250,7 @@ lbm_status run_steps(lbm_handle h, int64_t n, bool obs) {
         it = h->graphs.emplace(key, ex).first;
     }
     CK(h, cudaGraphLaunch(it->second, h->st));
-    if (n & 1) h->cur ^= 1;
+    if (pull_steps(h, n, obs) & 1) h->cur ^= 1;
     return LBM_OK;
 }
 
@@ -342,6 +366,7 @@ void lbm_options_default(lbm_options* o) {
     o->cancel_flag = nullptr;
     o->strip_rows = 0;
     o->k_tol = 1e-5;
+    o->in_place_pairs = 1;
 }
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
@@ -400,7 +425,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     }
     if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) || !(o.k_tol >= 0.0) ||
         (o.equilibrium != LBM_EQ_QUADRATIC && o.equilibrium != LBM_EQ_LINEAR) || o.block_threads < 0 ||
-        o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255)
+        o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255 ||
+        (o.in_place_pairs != 0 && o.in_place_pairs != 1))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     int q = force_q;
     if (!q) {
@@ -424,7 +450,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         segs += (uint64_t)((D.nx + kSegW - 1) / kSegW) * D.ny * D.nz;
         cells += N;
     }
-    if (segs >= (1ull << 32) || (cells + 32) * q >= (1ull << 32) || n >= (1 << 24))
+    if (segs >= (1ull << 32) || (cells + 32ull * (n + 2)) * q >= (1ull << 32) || n >= (1 << 24))
         return fail(nullptr, LBM_ERR_ARG, "batch too large (Q x nodes must stay below 2^32)");
 
     lbm_handle h = new lbm_solver();
@@ -513,9 +539,36 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(cudaStreamSynchronize(h->st));
     off[sb] = total;
     h->nfluid = total;
-    for (int d = 0; d < n; ++d) {
-        h->dom[d].fluid_begin = off[begin[d]];
-        h->dom[d].fluid_count = off[begin[d + 1]] - off[begin[d]];
+    // Each domain's compact range starts on a 32-slot boundary, so that the
+    // local step of the in-place pair moves whole aligned vectors; the slots
+    // in between belong to no node and stay zero.
+    {
+        uint32_t pos = 0;
+        for (int d = 0; d < n; ++d) {
+            const uint32_t b0 = off[begin[d]], cnt = off[begin[d + 1]] - b0;
+            const uint32_t nb = (pos + 31u) / 32u * 32u;
+            for (uint32_t g = begin[d]; g < begin[d + 1]; ++g) off[g] = off[g] - b0 + nb;
+            h->dom[d].fluid_begin = nb;
+            h->dom[d].fluid_count = cnt;
+            h->hdom[d].fluid_begin = nb;
+            h->hdom[d].fluid_end = nb + cnt;
+            pos = nb + cnt;
+        }
+        total = (pos + 31u) / 32u * 32u;
+        off[sb] = total;
+        CKC(cudaMemcpyAsync(h->d_seg_off, off.data(), sizeof(uint32_t) * sb, cudaMemcpyHostToDevice, h->st));
+    }
+    // local-step work items: 32 lanes x V slots of one domain each
+    {
+        const uint32_t span = 32u * (uint32_t)local_step_vector(q);
+        std::vector<uint2> vit;
+        for (int d = 0; d < n; ++d)
+            for (uint32_t k = h->hdom[d].fluid_begin; k < h->hdom[d].fluid_end; k += span)
+                vit.push_back(make_uint2(k, (uint32_t)d));
+        h->nvitems = (uint32_t)vit.size();
+        CKC(cudaMalloc(&h->d_vitems, sizeof(uint2) * std::max<size_t>(vit.size(), 1)));
+        CKC(cudaMemcpyAsync(h->d_vitems, vit.data(), sizeof(uint2) * vit.size(), cudaMemcpyHostToDevice, h->st));
+        CKC(cudaStreamSynchronize(h->st));
     }
     // Strip work list: per domain and z plane, runs of up to R rows at each
     // segment column, with the column innermost so that warps of one block (and
@@ -550,6 +603,9 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     // one padding slot past the last fluid node: the stream-collide kernel
     // loads unconditionally and a solid lane may address slot nfluid
     h->pstride = ((uint64_t)total + 1 + 31) / 32 * 32;
+    CKC(cudaMalloc(&h->d_face, sizeof(uint32_t) * (h->pstride / 16)));
+    CKC(cudaMemsetAsync(h->d_face, 0, sizeof(uint32_t) * (h->pstride / 16), h->st));
+    CKC(launch_build_face(h->d_dom, h->d_seg_dom, sb, h->d_seg_mask, h->d_seg_off, h->d_face, h->st));
     const int D = (q == 9) ? 2 : 3;
     CKC(cudaMalloc(&h->d_g[0], sizeof(float) * q * h->pstride));
     CKC(cudaMalloc(&h->d_g[1], sizeof(float) * q * h->pstride));
@@ -557,6 +613,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(cudaMalloc(&h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
     CKC(cudaMalloc(&h->d_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
+    CKC(cudaMemsetAsync(h->d_g[0], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(launch_init(q, h->geom(), h->d_g[0], h->d_uprev, h->st));
     CKC(cudaStreamSynchronize(h->st));

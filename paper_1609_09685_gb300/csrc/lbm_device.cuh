@@ -72,6 +72,8 @@ struct DomainDev {
     uint64_t mask_base;  // byte offset of the domain's dense mask
     uint32_t item_base;  // first strip work item of the domain
     uint32_t nitems;     // strip work items of the domain
+    uint32_t fluid_begin;  // compact index of the domain's first fluid node (a multiple of 32)
+    uint32_t fluid_end;    // one past its last fluid node
 };
 
 // Neighbour window of one segment, read by the stream-collide kernel:
@@ -97,6 +99,9 @@ struct HotArgs {
     uint32_t pstride;        // elements between direction planes (Q * pstride < 2^32)
     const float* src[19];    // direction planes of the state being read
     float* dst[19];          // direction planes of the state being written
+    const uint2* vitems;     // local-step work items: (first compact index, domain), one warp each
+    uint32_t nvitems;
+    const uint32_t* face;    // 2 bits per compact slot: bit 0 inlet (x = 0), bit 1 outlet (x = N_x - 1)
 };
 
 // Arguments shared by every segment kernel.

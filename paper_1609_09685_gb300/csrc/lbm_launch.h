@@ -11,6 +11,13 @@ namespace lbmgb {
 
 cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const float* src, float* dst,
                                   float* uprev, double* partials, int threads, cudaStream_t st);
+// Two steps in place on g (gather step, then local step); see k_aa_gather.
+cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, cudaStream_t st);
+// Slots per lane of the local step (its work items cover 32 x this many slots).
+int local_step_vector(int q);
+// Inlet/outlet bits of the compact slots (face zeroed beforehand).
+cudaError_t launch_build_face(const DomainDev* dom, const uint32_t* seg_dom, uint32_t nseg_total,
+                              const uint32_t* seg_mask, const uint32_t* seg_off, uint32_t* face, cudaStream_t st);
 cudaError_t launch_build_windows(const DomainDev* dom, const uint32_t* seg_dom, uint32_t nseg_total,
                                  const uint32_t* seg_mask, const uint32_t* seg_off, uint4* win,
                                  cudaStream_t st);

@@ -56,6 +56,7 @@ class lbm_options(C.Structure):
         ("cancel_flag", C.c_void_p),
         ("strip_rows", C.c_int32),
         ("k_tol", C.c_double),
+        ("in_place_pairs", C.c_int32),
     ]
 
 
@@ -163,7 +164,8 @@ def current_stream() -> Optional[int]:
 
 def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=200,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
-                 use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5) -> lbm_options:
+                 use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
+                 in_place_pairs=True) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -177,6 +179,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.cancel_flag = cancel_flag
     o.strip_rows = strip_rows
     o.k_tol = k_tol
+    o.in_place_pairs = 1 if in_place_pairs else 0
     return o
 
 

@@ -5,7 +5,8 @@ At these sizes the oracle cannot run to steady state within a test, so the
 check is one-step consistency on sampled domains: after the GPU has advanced
 the batch, the oracle takes one FP64 step from the GPU's own populations and
 the GPU's next step must agree within the FP32 bound used throughout
-(|g_gpu - g_oracle| <= 2e-6 max|g|).  Converged permeabilities are compared
+(|g_gpu - g_oracle| <= 2e-6 max|g| per step; two steps run as one in-place
+pair).  Converged permeabilities are compared
 against cold oracle runs at moderate sizes.
 """
 import numpy as np
@@ -35,18 +36,20 @@ def _masks(wl):
     return masks
 
 
-def _one_step_check(s, masks, wl, d, eq=0):
+def _one_step_check(s, masks, wl, d, eq=0, nsteps=1):
+    """nsteps = 1: one pull step; nsteps = 2: one in-place pair (the form the
+    bench's plain steps take), checked against two FP64 oracle steps."""
     q = s.q
     w = O.lattice(q)[1]
     f = lbm.lbm_get_populations(s, d)
     dom = wl.domains[d]
-    ref = O.step(masks[d], f, dom.tau, 1.0 + dom.drho, 1.0, eq)
-    lbm.lbm_step(s, 1)
+    ref = O.run(masks[d], f, dom.tau, 1.0 + dom.drho, 1.0, nsteps, eq)
+    lbm.lbm_step(s, nsteps)
     g = lbm.lbm_get_populations(s, d)
     fluid = ~masks[d].astype(bool)
     a, b = (g - w)[fluid], (ref - w)[fluid]
     err, scale = np.abs(a - b).max(), np.abs(b).max()
-    assert err <= REL * scale, (d, err, scale)
+    assert err <= nsteps * REL * scale, (d, err, scale)
     return f, g
 
 
@@ -60,6 +63,8 @@ def test_tau_sweep_batch_one_step_parity_full_size():
         # sampled domains: smallest and largest tau at each resolution
         for d in (0, 7, 8, 15, 16, 23):
             _one_step_check(s, masks, wl, d)
+        for d in (0, 15, 23):
+            _one_step_check(s, masks, wl, d, nsteps=2)
         # the other domains advanced by the same step stay bit-identical to an
         # untouched replay of the batch: compare one more domain after stepping
         k, kn = lbm.lbm_permeability(s)
@@ -73,6 +78,7 @@ def test_d3q19_full_size_one_step_parity():
     with lbm.lbm_batch_create(masks, [d.tau for d in wl.domains], [d.drho for d in wl.domains]) as s:
         lbm.lbm_step(s, 40)
         _one_step_check(s, masks, wl, 0)
+        _one_step_check(s, masks, wl, 0, nsteps=2)
 
 
 def test_batch128_sampled_one_step_parity():
@@ -83,6 +89,8 @@ def test_batch128_sampled_one_step_parity():
         lbm.lbm_step(s, 30)
         for d in (0, 17, 64, 127):
             _one_step_check(s, masks, wl, d)
+        for d in (5, 127):
+            _one_step_check(s, masks, wl, d, nsteps=2)
 
 
 @pytest.mark.parametrize("shape,tau", [((100, 200), 0.6), ((60, 120), 1.5)])
