@@ -172,14 +172,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, q: int):
-    """DRAM bytes per stream-collide launch from the committed ncu summary, if it
-    was taken on the current kernel source."""
+def profiled_traffic(workload: str, q: int, kind: str):
+    """DRAM bytes per launch of one kernel kind from the committed ncu summary,
+    if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
-        e = d[f"{workload}_q{q}"]
+        e = d[f"{workload}_q{q}_{kind}"]
         if e.get("kernel_hash") != kernel_source_hash():
             return None
         return float(e["dram_bytes_per_launch"])
@@ -415,7 +415,29 @@ def run_native(args):
         clocks = sampler.stop()
     t = e0.elapsed_time(e1) / 1e3
     t_kern = sum(a.elapsed_time(b) for a, b in zip(ka, kb)) / 1e3 / (args.steps * (N - 1))
-    (t, t_kern), (updates,) = combine_ranks(dist, "cuda", [t, t_kern], [float(args.steps * N * fluid)])
+
+    # Per-kernel device times: the same K intervals once more, with the plain
+    # steps launched one by one between CUDA events on the solver's stream
+    # (lbm_profile_steps) instead of through the cached graph.
+    with torch.cuda.stream(stream):
+        barrier()
+        kt = {k: [0.0, 0] for k in lbm.KERNEL_KINDS}
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for k in range(args.steps):
+            prof = lbm.lbm_profile_steps(s, N - 1)
+            for kind, (us, cnt) in prof.items():
+                kt[kind][0] += us
+                kt[kind][1] += cnt
+            lbm.lbm_step_observe(s, 1)
+        p1.record(stream)
+        barrier()
+    t_prof = p0.elapsed_time(p1) / 1e3
+    kinds = [k for k in lbm.KERNEL_KINDS if kt[k][1] > 0]
+    avg_us = [kt[k][0] / kt[k][1] for k in kinds]
+    (t, t_kern, t_prof, *avg_us), (updates,) = combine_ranks(
+        dist, "cuda", [t, t_kern, t_prof] + avg_us, [float(args.steps * N * fluid)])
     value = updates / t / 1e6
 
     # end to end through the C ABI: host masks (pinned) -> create -> one interval
@@ -445,7 +467,21 @@ def run_native(args):
 
     if rank == 0:
         peak, peak_src = measured_hbm_peak()
-        achieved = bytes_per_launch / t_kern / 1e9
+        achieved_step = bytes_per_launch / t_kern / 1e9
+        names = {"gather": "k_aa_gather (gather step of the in-place pair)",
+                 "local": "k_aa_local (local step of the in-place pair)",
+                 "pull": "k_stream_collide (pull step)"}
+        kernels = {}
+        for kind, us in zip(kinds, avg_us):
+            a = bytes_per_launch / (us * 1e-6) / 1e9
+            kernels[kind] = {"kernel": names.get(kind, kind), "launches_per_interval": kt[kind][1] // args.steps,
+                             "avg_launch_us": us, "achieved": a, "frac": a / peak,
+                             "traffic": profiled_traffic(args.workload, q, kind)}
+        total_us = sum(v["avg_launch_us"] * v["launches_per_interval"] for v in kernels.values())
+        for v in kernels.values():
+            v["share_of_plain_steps"] = v["avg_launch_us"] * v["launches_per_interval"] / total_us
+        dom_kind = max(kernels, key=lambda k: kernels[k]["share_of_plain_steps"])
+        dk = kernels[dom_kind]
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = oracle_sample(wl, args.cpu_seconds)
@@ -464,15 +500,23 @@ def run_native(args):
                 "l2": f"inputs larger than L2: {2 * 4 * q * fluid / 1e9:.2f} GB of populations per step",
                 "parallelism": f"independent domains, one replica per GPU ({world})",
             },
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(args.workload, q),
-                         "kernel": "k_stream_collide", "bytes_per_launch": bytes_per_launch,
-                         "algorithmic_bytes": f"{2 * 4 * q} B per fluid-node update",
-                         "avg_launch_us": t_kern * 1e6, "peak_source": peak_src},
+            "roofline": {"bound": "hbm", "achieved": dk["achieved"], "peak": peak, "unit": "GB/s",
+                         "frac": dk["frac"], "traffic": dk["traffic"],
+                         "kernel": dk["kernel"], "bytes_per_launch": bytes_per_launch,
+                         "algorithmic_bytes": f"{2 * 4 * q} B per fluid-node update (one step)",
+                         "avg_launch_us": dk["avg_launch_us"], "peak_source": peak_src,
+                         "timing": "CUDA events around every kernel on the solver's stream over the "
+                                   f"{args.steps} intervals of the per-kernel pass (lbm_profile_steps)",
+                         "kernels": kernels,
+                         "plain_step_average": {"avg_step_us": t_kern * 1e6, "achieved": achieved_step,
+                                                "frac": achieved_step / peak,
+                                                "timing": "CUDA events around the graph-launched plain "
+                                                          "steps of the timed region"}},
             "e2e": {"value": e2e_updates / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "step": "create from pinned host masks + one interval + permeability readback"},
-            "gpu_launches": args.steps * (N + 1),
+            "gpu_launches": args.steps * (sum(kt[k][1] for k in kinds) // args.steps + 2),
+            "ms_per_step_per_kernel_pass": t_prof / args.steps * 1e3,
             "clocks": clocks,
         }
         if cpu is not None:

@@ -170,6 +170,22 @@ lbm_status lbm_domain_fluid_nodes(lbm_handle h, int32_t d, int64_t* fluid_nodes)
 lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 
 /*
+ * Measurement: advance nsteps plain steps exactly as lbm_step does (same
+ * kernels, same pairing), but launch every kernel on its own with a CUDA event
+ * recorded before and after it on the solver's stream, instead of through the
+ * cached graph.  On return (the call synchronises) times_us[k] holds the summed
+ * device time in microseconds and counts[k] the launches of each kernel kind
+ * k: LBM_KERNEL_GATHER (the gather step of an in-place pair),
+ * LBM_KERNEL_LOCAL (its local step), LBM_KERNEL_PULL (a pull step),
+ * LBM_KERNEL_PULL_OBSERVE (unused here: always 0).  Both arrays are host
+ * memory of LBM_NUM_KERNEL_KINDS entries; nsteps is at most 100000.
+ * No counterpart in the paper (a timing aid for the kernels of Sec. 2's step).
+ */
+enum { LBM_KERNEL_GATHER = 0, LBM_KERNEL_LOCAL = 1, LBM_KERNEL_PULL = 2, LBM_KERNEL_PULL_OBSERVE = 3,
+       LBM_NUM_KERNEL_KINDS = 4 };
+lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int64_t* counts);
+
+/*
  * Enqueue nsteps steps of which the last also reduces, per domain, in FP64:
  *   obs[d*8 + 0] = sum over the N_x - 1 interior planes x + 1/2 of the mass
  *                  crossing each plane in the next streaming (the link flux

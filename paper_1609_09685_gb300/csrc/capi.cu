@@ -197,23 +197,56 @@ int64_t pull_steps(lbm_handle h, int64_t n, bool obs) {
     return o + (h->opt.in_place_pairs ? (plain & 1) : plain);
 }
 
+// Per-kernel timing for lbm_profile_steps: an event pair around every launch.
+struct KernelProf {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    cudaError_t mark(cudaStream_t st) {
+        cudaEvent_t e = nullptr;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+        return cudaEventRecord(e, st);
+    }
+    ~KernelProf() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 // Enqueue n steps (the last one observing when obs) plus the reduction and the
 // copy of the observables to pinned host memory.  Plain steps run as in-place
 // pairs on the current buffer (when enabled); the remaining steps pull from
-// the current buffer into the other one.  Advances h->cur.
-lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs) {
+// the current buffer into the other one.  Advances h->cur.  With prof, every
+// kernel is bracketed by events (kinds: 0 gather, 1 local, 2 pull, 3 observing
+// pull).
+lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = nullptr) {
     const Geometry G = h->geom();
     const HotArgs A = h->hot();
     const int64_t o = (obs && n > 0) ? 1 : 0;
     int64_t plain = n - o;
     if (h->opt.in_place_pairs) {
-        for (; plain >= 2; plain -= 2)
-            CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+        for (; plain >= 2; plain -= 2) {
+            if (!prof) {
+                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+                continue;
+            }
+            for (int half = 0; half < 2; ++half) {
+                CK(h, prof->mark(h->st));
+                CK(h, launch_aa_half(h->q, h->eq, half, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+                CK(h, prof->mark(h->st));
+                prof->kind.push_back(half);
+            }
+        }
     }
     for (int64_t k = 0; k < plain + o; ++k) {
         const bool ob = (o == 1) && (k == plain);
+        if (prof) CK(h, prof->mark(h->st));
         CK(h, launch_stream_collide(h->q, h->eq, ob, A, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
                                     h->d_partials, h->opt.block_threads, h->st));
+        if (prof) {
+            CK(h, prof->mark(h->st));
+            prof->kind.push_back(ob ? 3 : 2);
+        }
         h->cur ^= 1;
     }
     if (obs) {
@@ -669,6 +702,31 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
             if (D.active) D.has_obs = false;
     }
     return s;
+}
+
+lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int64_t* counts) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (nsteps < 0 || nsteps > 100000) return fail(h, LBM_ERR_ARG, "nsteps must be in [0, 100000]");
+    if (!times_us || !counts) return fail(h, LBM_ERR_ARG, "times_us and counts are required");
+    for (int k = 0; k < LBM_NUM_KERNEL_KINDS; ++k) {
+        times_us[k] = 0.0;
+        counts[k] = 0;
+    }
+    if (nsteps == 0) return LBM_OK;
+    KernelProf prof;
+    lbm_status s = enqueue_steps(h, nsteps, false, &prof);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->st));
+    for (size_t i = 0; i < prof.kind.size(); ++i) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, prof.ev[2 * i], prof.ev[2 * i + 1]));
+        times_us[prof.kind[i]] += 1e3 * (double)ms;
+        counts[prof.kind[i]] += 1;
+    }
+    h->step += nsteps;
+    for (auto& D : h->dom)
+        if (D.active) D.has_obs = false;
+    return LBM_OK;
 }
 
 lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {

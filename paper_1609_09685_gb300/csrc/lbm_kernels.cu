@@ -1421,9 +1421,10 @@ cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const floa
 }
 
 template <class L, int EQ>
-static cudaError_t aa_pair_launch(int threads, const HotArgs& A, cudaStream_t st) {
-    const unsigned nb = seg_blocks(A.nitems, threads);
-    if (nb > 0) {
+static cudaError_t aa_half_launch(int half, int threads, const HotArgs& A, cudaStream_t st) {
+    if (half == 0) {
+        const unsigned nb = seg_blocks(A.nitems, threads);
+        if (nb == 0) return cudaSuccess;
         if ((L::Q == 9) ? LBM_AA_GATHER_PIPE_2D : LBM_AA_GATHER_PIPE_3D) {
             void (*kern)(HotArgs);
             if constexpr (L::Q == 9) kern = k_aa_gather_pipe2<L, EQ>;
@@ -1441,22 +1442,28 @@ static cudaError_t aa_pair_launch(int threads, const HotArgs& A, cudaStream_t st
         } else {
             k_aa_gather3<L, EQ><<<nb, threads, 0, st>>>(A);
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
     }
     const unsigned nv = seg_blocks(A.nvitems, threads);
     if (nv > 0) k_aa_local<L, EQ><<<nv, threads, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, cudaStream_t st) {
+cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, int threads, cudaStream_t st) {
     if (threads <= 0) threads = 128;
     for (int i = 0; i < 19; ++i) {
         A.dst[i] = i < q ? g + (size_t)i * A.pstride : nullptr;
         A.src[i] = A.dst[i];
     }
-    if (q == 9) return eq == 0 ? aa_pair_launch<D2Q9, 0>(threads, A, st) : aa_pair_launch<D2Q9, 1>(threads, A, st);
-    return eq == 0 ? aa_pair_launch<D3Q19, 0>(threads, A, st) : aa_pair_launch<D3Q19, 1>(threads, A, st);
+    if (q == 9)
+        return eq == 0 ? aa_half_launch<D2Q9, 0>(half, threads, A, st) : aa_half_launch<D2Q9, 1>(half, threads, A, st);
+    return eq == 0 ? aa_half_launch<D3Q19, 0>(half, threads, A, st) : aa_half_launch<D3Q19, 1>(half, threads, A, st);
+}
+
+cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, cudaStream_t st) {
+    cudaError_t e = launch_aa_half(q, eq, 0, A, g, threads, st);
+    if (e != cudaSuccess) return e;
+    return launch_aa_half(q, eq, 1, A, g, threads, st);
 }
 
 int local_step_vector(int q) { return q == 9 ? LocalVec<D2Q9>::value : LocalVec<D3Q19>::value; }

@@ -104,6 +104,7 @@ def load(path: Optional[str] = None):
         "lbm_domain_fluid_nodes": (i32, [P, i32, P]),
         "lbm_step": (i32, [P, i64]),
         "lbm_step_observe": (i32, [P, i64, P]),
+        "lbm_profile_steps": (i32, [P, i64, P, P]),
         "lbm_run_to_steady": (i32, [P, d, i64, P, P, P]),
         "lbm_permeability": (i32, [P, P, P]),
         "lbm_get_fields": (i32, [P, i32, P, P, P, P]),
@@ -311,6 +312,18 @@ def lbm_step_observe(s: Solver, nsteps: int) -> np.ndarray:
     out = np.zeros((s.n_domains, NUM_OBS), np.float64)
     _check(load().lbm_step_observe(s.handle, int(nsteps), _ptr(out)), s.handle)
     return out
+
+
+KERNEL_KINDS = ("gather", "local", "pull", "pull_observe")
+
+
+def lbm_profile_steps(s: Solver, nsteps: int) -> dict:
+    """nsteps plain steps with CUDA events around every kernel; returns
+    {kind: (total device microseconds, launches)}."""
+    t = np.zeros(len(KERNEL_KINDS), np.float64)
+    c = np.zeros(len(KERNEL_KINDS), np.int64)
+    _check(load().lbm_profile_steps(s.handle, int(nsteps), _ptr(t), _ptr(c)), s.handle)
+    return {k: (float(t[i]), int(c[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def lbm_run_to_steady(s: Solver, tol: float, max_steps: int):

@@ -80,8 +80,20 @@ def test_create_rejects_non_binary_mask(lib):
     assert "0 (fluid) or 1 (solid)" in lib.lbm_last_error(None).decode()
 
 
+def test_create_rejects_bad_in_place_pairs_option(lib):
+    o = lbm.make_options()
+    o.in_place_pairs = 2
+    h = C.c_void_p()
+    m = np.zeros((6, 9), np.uint8)
+    assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+    assert h.value is None
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    t = np.zeros(4)
+    c = np.zeros(4, np.int64)
+    assert lib.lbm_profile_steps(None, 2, t.ctypes.data, c.ctypes.data) == lbm.LBM_ERR_ARG
     assert lib.lbm_run_to_steady(None, 1e-9, 10, None, None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_permeability(None, None, None) == lbm.LBM_ERR_ARG
 

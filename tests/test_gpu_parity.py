@@ -196,6 +196,21 @@ def test_in_place_pairs_match_pull_steps(dim):
         assert np.abs(da - db).max() <= 1e-6 * np.abs(db).max()
 
 
+def test_profile_steps_runs_the_same_steps_with_per_kernel_times():
+    """lbm_profile_steps advances the state exactly as lbm_step does (the same
+    kernels, launched one by one with events around them) and reports one
+    gather and one local launch per pair and a pull launch for the odd step."""
+    mask, _ = O.qsgs((30, 90), 8, 0.02, 0.72)
+    with lbm.lbm_create_domain(mask, 0.8, 1e-3) as a, lbm.lbm_create_domain(mask, 0.8, 1e-3) as b:
+        lbm.lbm_step(a, 7)
+        prof = lbm.lbm_profile_steps(b, 7)
+        assert np.array_equal(lbm.lbm_get_populations(a, 0), lbm.lbm_get_populations(b, 0))
+        assert lbm.lbm_get_step(b) == 7
+    assert prof["gather"][1] == 3 and prof["local"][1] == 3 and prof["pull"][1] == 1
+    assert prof["pull_observe"] == (0.0, 0)
+    assert all(prof[k][0] > 0 for k in ("gather", "local", "pull"))
+
+
 def test_rest_state_is_exactly_zero_on_device():
     mask, _ = O.qsgs((30, 70), 4, 0.02, 0.7)
     with lbm.lbm_create_domain(mask, 0.7, 0.0) as s:
