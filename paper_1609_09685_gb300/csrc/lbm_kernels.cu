@@ -584,7 +584,7 @@ __device__ __forceinline__ void src_elems(uint32_t (&e)[L::Q], const Win (&w)[L:
 #define LBM_AA_GATHER_REGS_2D 80
 #endif
 #ifndef LBM_AA_GATHER_REGS_3D
-#define LBM_AA_GATHER_REGS_3D 128
+#define LBM_AA_GATHER_REGS_3D 96
 #endif
 #ifndef LBM_AA_MINB_LOCAL
 #define LBM_AA_MINB_LOCAL 3
@@ -677,26 +677,144 @@ __device__ __forceinline__ void aa_gather_body(const HotArgs& A) {
     }
 }
 
+// Gather step with the source slots parked in shared memory: a batch of RS
+// rows keeps only its loaded values in registers, so more rows of loads are in
+// flight per warp at the same register budget.
+#ifndef LBM_AA_GATHER_SMEM_2D
+#define LBM_AA_GATHER_SMEM_2D 1
+#endif
+#ifndef LBM_AA_SMEM_ROWS_2D
+#define LBM_AA_SMEM_ROWS_2D 4
+#endif
+#ifndef LBM_AA_GATHER_SMEM_3D
+#define LBM_AA_GATHER_SMEM_3D 1
+#endif
+#ifndef LBM_AA_SMEM_ROWS_3D
+#define LBM_AA_SMEM_ROWS_3D 2
+#endif
+template <class L>
+struct GatherSmem {
+    static constexpr bool on = (L::Q == 9) ? LBM_AA_GATHER_SMEM_2D : LBM_AA_GATHER_SMEM_3D;
+    static constexpr int rows = (L::Q == 9) ? LBM_AA_SMEM_ROWS_2D : LBM_AA_SMEM_ROWS_3D;
+};
+template <class L, int EQ, int RS>
+__device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
+    constexpr int Q = L::Q;
+    constexpr int NZ = (L::NROW == 9) ? 3 : 1;
+    extern __shared__ uint32_t sme[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (item >= A.nitems) return;
+    const uint4 it = __ldg(A.items + item);
+    const uint32_t dom = it.y & 0xffffffu;
+    const int nrows = (int)(it.y >> 24);
+    const DomainDev D = A.dom[dom];
+    if (!D.active) return;
+    const int y0 = (int)(it.z & 0xffffu), z = (int)(it.z >> 16);
+    const int x = (int)it.w * kSegW + lane;
+    const uint32_t lmask = (1u << lane) - 1u;
+    const uint32_t PS = A.pstride;
+    const int ny = D.ny;
+    const bool zlo = (z == 0), zhi = (z == D.nz - 1);
+    const bool xin = (x == 0), xout = (x == D.nx - 1);
+    const bool edge = (it.w == 0) || ((int)it.w == D.nseg - 1);
+    float* const g = A.dst[0];
+    volatile uint32_t* const we = sme + (size_t)wid * RS * Q * 32 + lane;
+    const SegWindow* wcol = A.win + D.seg_base + it.w;
+    const uint32_t rs = (uint32_t)D.nseg;
+    uint32_t pbase[NZ];
+#pragma unroll
+    for (int zi = 0; zi < NZ; ++zi) {
+        int zz = z + zi - (NZ == 3 ? 1 : 0);
+        zz = zz < 0 ? 0 : (zz >= D.nz ? D.nz - 1 : zz);
+        pbase[zi] = (uint32_t)zz * (uint32_t)ny;
+    }
+    auto rowc = [&](int yy) { return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy); };
+    constexpr bool kSlide = (NZ == 1);
+    Win wm, wc, wp;
+    if (kSlide) {
+        wm = make_win(__ldg(wcol + (pbase[0] + rowc(y0 - 1)) * rs), lane, lmask);
+        wc = make_win(__ldg(wcol + (pbase[0] + y0) * rs), lane, lmask);
+    }
+#pragma unroll 1
+    for (int r0 = 0; r0 < nrows; r0 += RS) {
+        float f[RS][Q];
+        uint32_t flb = 0u;
+#pragma unroll
+        for (int j = 0; j < RS; ++j) {
+            // rows past the strip's end repeat its last row: the loads stay in
+            // bounds and nothing is stored for them
+            const int y = y0 + min(r0 + j, nrows - 1);
+            Win w[L::NROW];
+            if (kSlide) {
+                wp = make_win(__ldg(wcol + (pbase[0] + rowc(y + 1)) * rs), lane, lmask);
+                w[0] = wm;
+                w[1] = wc;
+                w[2] = wp;
+                if (r0 + j + 1 < nrows) {
+                    wm = wc;
+                    wc = wp;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < L::NROW; ++q) {
+                    const int zi = q / 3, dy = q % 3 - 1;
+                    w[q] = make_win(__ldg(wcol + (pbase[zi] + rowc(y + dy)) * rs), lane, lmask);
+                }
+            }
+            constexpr int C = (L::NROW == 9) ? 4 : 1;
+            if (win_fluid<0>(w[C]) && (r0 + j < nrows)) flb |= 1u << j;
+            // a solid lane's kd is the next fluid slot (at most the padding
+            // slot), so every read is in bounds; its values are discarded
+            uint32_t e[Q];
+            src_elems<L>(e, w, PS, win_idx<0>(w[C]), y == 0, y == ny - 1, zlo, zhi,
+                         std::make_integer_sequence<int, Q>{});
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[j][i] = g[e[i]];
+                we[(j * Q + i) * 32] = e[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RS; ++j) {
+            relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega);
+            if ((flb >> j) & 1u) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[we[(j * Q + opp<L>(i)) * 32]] = f[j][i];
+            }
+        }
+    }
+}
+template <class L>
+constexpr size_t gather_smem_bytes(int threads) {
+    return GatherSmem<L>::on ? (size_t)(threads / 32) * GatherSmem<L>::rows * L::Q * 32 * sizeof(uint32_t) : 0;
+}
+
 template <class L, int EQ>
 __global__ void __maxnreg__(LBM_AA_GATHER_REGS_2D) k_aa_gather2(const __grid_constant__ HotArgs A) {
-    aa_gather_body<L, EQ>(A);
+    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, GatherSmem<L>::rows>(A);
+    else aa_gather_body<L, EQ>(A);
 }
 template <class L, int EQ>
 __global__ void __maxnreg__(LBM_AA_GATHER_REGS_3D) k_aa_gather3(const __grid_constant__ HotArgs A) {
-    aa_gather_body<L, EQ>(A);
+    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, GatherSmem<L>::rows>(A);
+    else aa_gather_body<L, EQ>(A);
 }
 
 // Gather step, pipelined: the pull kernel's row pipeline (rows k+1 .. k+S-1
 // in flight as cp.async copies into the warp's shared-memory stages while row
 // k is relaxed), with each row's source slots kept in registers until its
 // results are written back to them.
-// Measured on GB300: the direct-load form is faster for D2Q9, the pipelined
-// form for D3Q19.
+// Gather forms, measured on GB300 (us per step on the D2Q9 tau sweep / one
+// D3Q19 256x128x128 pair of domains): slots parked in shared memory
+// 90.4 / 183.4 (the default for both), slots in registers 95.3 / 207.9,
+// cp.async pipeline 96.7 / 194.6.
 #ifndef LBM_AA_GATHER_PIPE_2D
 #define LBM_AA_GATHER_PIPE_2D 0
 #endif
 #ifndef LBM_AA_GATHER_PIPE_3D
-#define LBM_AA_GATHER_PIPE_3D 1
+#define LBM_AA_GATHER_PIPE_3D 0
 #endif
 #ifndef LBM_AA_PIPE_STAGES_2D
 #define LBM_AA_PIPE_STAGES_2D 3
@@ -1437,10 +1555,21 @@ static cudaError_t aa_half_launch(int half, int threads, const HotArgs& A, cudaS
                 attr_set = true;
             }
             kern<<<nb, threads, pipe_smem_bytes<L>(threads), st>>>(A);
-        } else if constexpr (L::Q == 9) {
-            k_aa_gather2<L, EQ><<<nb, threads, 0, st>>>(A);
         } else {
-            k_aa_gather3<L, EQ><<<nb, threads, 0, st>>>(A);
+            void (*kern)(HotArgs);
+            if constexpr (L::Q == 9) kern = k_aa_gather2<L, EQ>;
+            else kern = k_aa_gather3<L, EQ>;
+            const size_t sm = gather_smem_bytes<L>(threads);
+            if (GatherSmem<L>::on) {
+                static bool attr_set = false;  // per template instance
+                if (!attr_set) {
+                    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)gather_smem_bytes<L>(256));
+                    if (e != cudaSuccess) return e;
+                    attr_set = true;
+                }
+            }
+            kern<<<nb, threads, sm, st>>>(A);
         }
         return cudaGetLastError();
     }
