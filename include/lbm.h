@@ -159,6 +159,10 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, double
 lbm_status lbm_create_domain_3d(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz,
                                 double tau, double drho, const lbm_options* opt,
                                 lbm_handle* out);
+/* Synchronises the solver's stream and frees its resources.  Device memory of
+ * solvers comes from one stream-ordered pool per device; up to 8 GB of freed
+ * blocks stay cached there for the next solver, the rest returns to the
+ * driver at the next synchronisation. */
 void lbm_destroy(lbm_handle h);
 
 /* Number of domains, lattice size Q, and fluid node count of domain d. */

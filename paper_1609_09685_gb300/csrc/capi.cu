@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,7 +72,7 @@ struct lbm_solver {
     cudaStream_t st = nullptr;
     bool own_stream = false;
     std::vector<DomainHost> dom;
-    std::vector<uint8_t> masks;  // concatenated host masks (checkpoint)
+    uint64_t mask_bytes = 0;     // bytes of d_mask (all domains' dense masks)
     std::vector<DomainDev> hdom;
     DomainDev* d_dom = nullptr;
     uint32_t* d_dom_begin = nullptr;
@@ -144,26 +145,78 @@ lbm_status cuda_fail(lbm_handle h, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
     } while (0)
 
+// Device memory of solvers comes from one stream-ordered pool per device.  The
+// pool keeps up to kPoolKeep bytes of freed blocks, so creating and destroying
+// solvers in a loop reuses memory instead of returning it to the driver each
+// time; larger frees go back to the driver at the next synchronisation.
+constexpr uint64_t kPoolKeep = 8ull << 30;
+
+cudaError_t solver_pool(cudaMemPool_t* pool) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) {
+        *pool = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeep;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(p);
+        return e;
+    }
+    pools[dev] = p;
+    *pool = p;
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dmalloc(lbm_handle h, T** ptr, size_t bytes) {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = solver_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), bytes, pool, h->st);
+}
+
+template <class T>
+void dfree(lbm_handle h, T*& p) {
+    if (p) cudaFreeAsync(p, h->st);
+    p = nullptr;
+}
+
 void free_solver(lbm_handle h) {
     if (!h) return;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    cudaFree(h->d_dom);
-    cudaFree(h->d_dom_begin);
-    cudaFree(h->d_seg_dom);
-    cudaFree(h->d_seg_mask);
-    cudaFree(h->d_seg_off);
-    cudaFree(h->d_seg_cnt);
-    cudaFree(h->d_scan);
-    cudaFree(h->d_win);
-    cudaFree(h->d_items);
-    cudaFree(h->d_vitems);
-    cudaFree(h->d_face);
-    cudaFree(h->d_mask);
-    cudaFree(h->d_g[0]);
-    cudaFree(h->d_g[1]);
-    cudaFree(h->d_uprev);
-    cudaFree(h->d_partials);
-    cudaFree(h->d_obs);
+    if (h->st) {
+        dfree(h, h->d_dom);
+        dfree(h, h->d_dom_begin);
+        dfree(h, h->d_seg_dom);
+        dfree(h, h->d_seg_mask);
+        dfree(h, h->d_seg_off);
+        dfree(h, h->d_seg_cnt);
+        dfree(h, h->d_scan);
+        dfree(h, h->d_win);
+        dfree(h, h->d_items);
+        dfree(h, h->d_vitems);
+        dfree(h, h->d_face);
+        dfree(h, h->d_mask);
+        dfree(h, h->d_g[0]);
+        dfree(h, h->d_g[1]);
+        dfree(h, h->d_uprev);
+        dfree(h, h->d_partials);
+        dfree(h, h->d_obs);
+    }
     if (h->h_obs) cudaFreeHost(h->h_obs);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
@@ -478,8 +531,9 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         if (!std::isfinite(D.drho) || std::fabs(D.drho) >= o.rho_out)
             return fail(nullptr, LBM_ERR_ARG, "drho must be finite and |drho| < rho_out");
         const uint64_t N = (uint64_t)D.nx * D.ny * D.nz;
-        for (uint64_t k = 0; k < N; ++k)
-            if (D.mask[k] > 1) return fail(nullptr, LBM_ERR_ARG, "mask bytes must be 0 (fluid) or 1 (solid)");
+        uint8_t bad = 0;  // OR of the bits above bit 0 (a branch-free loop the compiler vectorises)
+        for (uint64_t k = 0; k < N; ++k) bad |= (uint8_t)(D.mask[k] & 0xFEu);
+        if (bad) return fail(nullptr, LBM_ERR_ARG, "mask bytes must be 0 (fluid) or 1 (solid)");
         segs += (uint64_t)((D.nx + kSegW - 1) / kSegW) * D.ny * D.nz;
         cells += N;
     }
@@ -530,9 +584,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.rho0 = (float)o.rho_out;
         G.active = 1;
         G.mask_base = mb;
-        const uint64_t N = (uint64_t)S.nx * S.ny * S.nz;
-        h->masks.insert(h->masks.end(), S.mask, S.mask + N);
-        mb += N;
+        mb += (uint64_t)S.nx * S.ny * S.nz;
         sb += D.nseg;
     }
     begin[n] = sb;
@@ -550,17 +602,20 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         }                                          \
     } while (0)
 
-    CKC(cudaMalloc(&h->d_dom, sizeof(DomainDev) * n));
-    CKC(cudaMalloc(&h->d_dom_begin, sizeof(uint32_t) * (n + 1)));
-    CKC(cudaMalloc(&h->d_seg_dom, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
-    CKC(cudaMalloc(&h->d_seg_mask, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
-    CKC(cudaMalloc(&h->d_seg_off, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
-    CKC(cudaMalloc(&h->d_seg_cnt, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
-    CKC(cudaMalloc(&h->d_scan, sizeof(uint32_t) * ((sb + 1023) / 1024 + 2)));
-    CKC(cudaMalloc(&h->d_mask, std::max<uint64_t>(mb, 1)));
+    CKC(dmalloc(h, &h->d_dom, sizeof(DomainDev) * n));
+    CKC(dmalloc(h, &h->d_dom_begin, sizeof(uint32_t) * (n + 1)));
+    CKC(dmalloc(h, &h->d_seg_dom, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(dmalloc(h, &h->d_seg_mask, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(dmalloc(h, &h->d_seg_off, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(dmalloc(h, &h->d_seg_cnt, sizeof(uint32_t) * std::max<uint32_t>(sb, 1)));
+    CKC(dmalloc(h, &h->d_scan, sizeof(uint32_t) * ((sb + 1023) / 1024 + 2)));
+    CKC(dmalloc(h, &h->d_mask, std::max<uint64_t>(mb, 1)));
     CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
     CKC(cudaMemcpyAsync(h->d_dom_begin, begin.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice, h->st));
-    CKC(cudaMemcpyAsync(h->d_mask, h->masks.data(), mb, cudaMemcpyHostToDevice, h->st));
+    h->mask_bytes = mb;
+    for (int d = 0; d < n; ++d)  // straight from the caller's buffers (DMA when they are pinned)
+        CKC(cudaMemcpyAsync(h->d_mask + h->hdom[d].mask_base, descs[d].mask,
+                            (size_t)descs[d].nx * descs[d].ny * descs[d].nz, cudaMemcpyHostToDevice, h->st));
     const uint32_t nscan = (sb + 1023) / 1024;
     CKC(launch_seg_setup(h->d_dom, h->d_dom_begin, n, sb, h->d_mask, h->d_seg_dom, h->d_seg_mask, h->d_seg_cnt,
                          h->d_seg_off, h->d_scan, h->d_scan + nscan + 1, h->st));
@@ -599,7 +654,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
             for (uint32_t k = h->hdom[d].fluid_begin; k < h->hdom[d].fluid_end; k += span)
                 vit.push_back(make_uint2(k, (uint32_t)d));
         h->nvitems = (uint32_t)vit.size();
-        CKC(cudaMalloc(&h->d_vitems, sizeof(uint2) * std::max<size_t>(vit.size(), 1)));
+        CKC(dmalloc(h, &h->d_vitems, sizeof(uint2) * std::max<size_t>(vit.size(), 1)));
         CKC(cudaMemcpyAsync(h->d_vitems, vit.data(), sizeof(uint2) * vit.size(), cudaMemcpyHostToDevice, h->st));
         CKC(cudaStreamSynchronize(h->st));
     }
@@ -627,24 +682,24 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.nitems = (uint32_t)items.size() - G.item_base;
     }
     h->nitems = (uint32_t)items.size();
-    CKC(cudaMalloc(&h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
+    CKC(dmalloc(h, &h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
     CKC(cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
     CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
-    CKC(cudaMalloc(&h->d_win, sizeof(uint4) * std::max<uint32_t>(sb, 1)));
+    CKC(dmalloc(h, &h->d_win, sizeof(uint4) * std::max<uint32_t>(sb, 1)));
     CKC(launch_build_windows(h->d_dom, h->d_seg_dom, sb, h->d_seg_mask, h->d_seg_off, h->d_win, h->st));
     CKC(cudaStreamSynchronize(h->st));
     // one padding slot past the last fluid node: the stream-collide kernel
     // loads unconditionally and a solid lane may address slot nfluid
     h->pstride = ((uint64_t)total + 1 + 31) / 32 * 32;
-    CKC(cudaMalloc(&h->d_face, sizeof(uint32_t) * (h->pstride / 16)));
+    CKC(dmalloc(h, &h->d_face, sizeof(uint32_t) * (h->pstride / 16)));
     CKC(cudaMemsetAsync(h->d_face, 0, sizeof(uint32_t) * (h->pstride / 16), h->st));
     CKC(launch_build_face(h->d_dom, h->d_seg_dom, sb, h->d_seg_mask, h->d_seg_off, h->d_face, h->st));
     const int D = (q == 9) ? 2 : 3;
-    CKC(cudaMalloc(&h->d_g[0], sizeof(float) * q * h->pstride));
-    CKC(cudaMalloc(&h->d_g[1], sizeof(float) * q * h->pstride));
-    CKC(cudaMalloc(&h->d_uprev, sizeof(float) * D * h->pstride));
-    CKC(cudaMalloc(&h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
-    CKC(cudaMalloc(&h->d_obs, sizeof(double) * kNumObs * n));
+    CKC(dmalloc(h, &h->d_g[0], sizeof(float) * q * h->pstride));
+    CKC(dmalloc(h, &h->d_g[1], sizeof(float) * q * h->pstride));
+    CKC(dmalloc(h, &h->d_uprev, sizeof(float) * D * h->pstride));
+    CKC(dmalloc(h, &h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
+    CKC(dmalloc(h, &h->d_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMemsetAsync(h->d_g[0], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));
@@ -1051,7 +1106,11 @@ lbm_status lbm_save(lbm_handle h, const char* path) {
         W(&ho, sizeof(ho));
         W(d.obs, sizeof(d.obs));
     }
-    W(h->masks.data(), h->masks.size());
+    {
+        std::vector<uint8_t> masks(h->mask_bytes);
+        CK(h, cudaMemcpy(masks.data(), h->d_mask, h->mask_bytes, cudaMemcpyDeviceToHost));
+        W(masks.data(), masks.size());
+    }
     std::vector<float> tmp;
     for (const DomainHost& d : h->dom) {
         tmp.resize((size_t)d.fluid_count);
