@@ -58,6 +58,17 @@ typedef enum {
 
 enum { LBM_EQ_QUADRATIC = 0, LBM_EQ_LINEAR = 1 };
 
+/*
+ * Collision.  BGK is the paper's single-relaxation model (Sec. 2, Eq. 1).  TRT
+ * (Ginzburg 2005) follows the paper's pointer to multi-relaxation models for a
+ * wall location that does not move with the viscosity: the parts of f - f_eq
+ * even and odd under i -> opp(i) relax with 1/tau (viscosity, as in BGK) and
+ * 1/tau_minus, tau_minus = 1/2 + Lambda/(tau - 1/2).  Steady states then
+ * depend on tau only through the viscosity; with Lambda = 3/16 a straight
+ * bounce-back wall sits exactly half way between nodes.
+ */
+enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 };
+
 /* Solver options.  Fill with lbm_options_default() and override fields. */
 typedef struct lbm_options {
     int32_t struct_size;     /* sizeof(lbm_options) */
@@ -75,6 +86,8 @@ typedef struct lbm_options {
     int32_t in_place_pairs;  /* 1 (default): advance plain steps two at a time in place (a gather step that
                                 writes each result back to the slot it read, then a step on each node's own
                                 slots); same arithmetic as two pull steps.  0: one pull step at a time. */
+    int32_t collision;       /* LBM_COLL_BGK (default) or LBM_COLL_TRT */
+    double trt_lambda;       /* TRT: Lambda = (tau - 1/2)(tau_minus - 1/2), > 0 (default 3/16) */
 } lbm_options;
 
 /* One domain of a batch. */

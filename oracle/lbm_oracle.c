@@ -218,10 +218,10 @@ static int check_dims(int q, int nx, int ny, int nz) {
  * Then Zou-He at fluid nodes of x = 0 and x = N_x - 1, moments, BGK relaxation
  * f* = f - (f - f_eq)/tau.
  */
-int oc_step(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
-            double rho_in, double rho_out, int eq, const double* fin, double* fout) {
+static int step_impl(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+                     int trt, double rho_in, double rho_out, int eq, const double* fin, double* fout) {
     lattice L;
-    if (get_lattice(q, &L) || check_dims(q, nx, ny, nz) || !(tau > 0.5)) return -1;
+    if (get_lattice(q, &L) || check_dims(q, nx, ny, nz) || !(tau > 0.5) || !(tau_minus > 0.5)) return -1;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -267,19 +267,51 @@ int oc_step(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
                 }
                 double rho, j[3];
                 moments(&L, f, &rho, j);
-                for (int i = 0; i < q; ++i) out[i] = f[i] - (f[i] - feq(&L, i, rho, j, eq)) / tau;
+                if (!trt) {
+                    for (int i = 0; i < q; ++i) out[i] = f[i] - (f[i] - feq(&L, i, rho, j, eq)) / tau;
+                } else {
+                    /* TRT: the parts of f and f_eq even and odd under i -> opp(i)
+                     * relax with 1/tau and 1/tau_minus respectively. */
+                    for (int i = 0; i < q; ++i) {
+                        const int o = L.opp[i];
+                        const double ei = feq(&L, i, rho, j, eq), eo = feq(&L, o, rho, j, eq);
+                        const double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+                        const double ep = 0.5 * (ei + eo), em = 0.5 * (ei - eo);
+                        out[i] = f[i] - (fp - ep) / tau - (fm - em) / tau_minus;
+                    }
+                }
             }
     return 0;
 }
 
-/* Run nsteps steps in place on f (uses a scratch buffer). */
-int oc_run(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double rho_in,
-           double rho_out, int eq, double* f, long nsteps) {
+int oc_step(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
+            double rho_in, double rho_out, int eq, const double* fin, double* fout) {
+    return step_impl(q, nx, ny, nz, solid, tau, tau, 0, rho_in, rho_out, eq, fin, fout);
+}
+
+/*
+ * Two-relaxation-time collision (Ginzburg 2005; the paper's Sec. 2 points to
+ * multi-relaxation models for a wall location independent of viscosity): the
+ * symmetric parts relax with tau (viscosity nu = (tau - 1/2)/3, as in BGK),
+ * the antisymmetric parts with tau_minus.  Steady solutions depend on tau and
+ * tau_minus only through Lambda = (tau - 1/2)(tau_minus - 1/2).
+ */
+int oc_step_trt(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+                double rho_in, double rho_out, int eq, const double* fin, double* fout) {
+    return step_impl(q, nx, ny, nz, solid, tau, tau_minus, 1, rho_in, rho_out, eq, fin, fout);
+}
+
+/* Run nsteps steps in place on f (uses a scratch buffer); tau_minus <= 0
+ * means BGK. */
+int oc_run_trt(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+               double rho_in, double rho_out, int eq, double* f, long nsteps) {
     long nn = (long)nx * ny * nz * q;
     double* tmp = (double*)malloc(sizeof(double) * nn);
     if (!tmp) return -2;
+    const int trt = tau_minus > 0.0;
     for (long t = 0; t < nsteps; ++t) {
-        int rc = oc_step(q, nx, ny, nz, solid, tau, rho_in, rho_out, eq, f, tmp);
+        int rc = step_impl(q, nx, ny, nz, solid, tau, trt ? tau_minus : tau, trt, rho_in, rho_out, eq, f,
+                           tmp);
         if (rc) {
             free(tmp);
             return rc;
@@ -288,6 +320,11 @@ int oc_run(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, doub
     }
     free(tmp);
     return 0;
+}
+
+int oc_run(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double rho_in,
+           double rho_out, int eq, double* f, long nsteps) {
+    return oc_run_trt(q, nx, ny, nz, solid, tau, 0.0, rho_in, rho_out, eq, f, nsteps);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -446,9 +483,9 @@ static double residual(const lattice* L, long nn, const uint8_t* solid, const do
 
 /* Iterate until the residual over `interval` steps is below tol, or max_steps.
  * Returns 0 when converged, 1 when max_steps was reached, <0 on error. */
-int oc_run_to_steady(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
-                     double rho_in, double rho_out, int eq, double* f, double tol,
-                     long max_steps, int interval, long* steps_out, double* res_out) {
+int oc_run_to_steady_trt(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+                         double rho_in, double rho_out, int eq, double* f, double tol,
+                         long max_steps, int interval, long* steps_out, double* res_out) {
     lattice L;
     if (get_lattice(q, &L) || interval < 1) return -1;
     long nn = (long)nx * ny * nz;
@@ -462,7 +499,7 @@ int oc_run_to_steady(int q, int nx, int ny, int nz, const uint8_t* solid, double
     while (t < max_steps) {
         long n = interval;
         if (t + n > max_steps) n = max_steps - t;
-        int e = oc_run(q, nx, ny, nz, solid, tau, rho_in, rho_out, eq, f, n);
+        int e = oc_run_trt(q, nx, ny, nz, solid, tau, tau_minus, rho_in, rho_out, eq, f, n);
         if (e) {
             rc = e;
             break;
@@ -482,6 +519,13 @@ int oc_run_to_steady(int q, int nx, int ny, int nz, const uint8_t* solid, double
     if (steps_out) *steps_out = t;
     if (res_out) *res_out = r;
     return rc;
+}
+
+int oc_run_to_steady(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
+                     double rho_in, double rho_out, int eq, double* f, double tol,
+                     long max_steps, int interval, long* steps_out, double* res_out) {
+    return oc_run_to_steady_trt(q, nx, ny, nz, solid, tau, 0.0, rho_in, rho_out, eq, f, tol, max_steps,
+                                interval, steps_out, res_out);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -32,7 +32,7 @@ __all__ = [
     "EQ_QUADRATIC", "EQ_LINEAR", "build", "lattice", "init", "step", "run",
     "equilibrium", "fields", "mean_jx", "permeability", "knudsen", "link_flux",
     "run_to_steady", "splitmix64", "qsgs_hash", "qsgs", "qsgs_grow_once", "percolates",
-    "Q_OF",
+    "Q_OF", "tau_minus",
 ]
 
 Q_OF = {2: 9, 3: 19}
@@ -60,6 +60,9 @@ def _get():
                 "oc_lattice": (i, [i, P, P, P]),
                 "oc_step": (i, [i, i, i, i, P, d, d, d, i, P, P]),
                 "oc_run": (i, [i, i, i, i, P, d, d, d, i, P, l]),
+                "oc_step_trt": (i, [i, i, i, i, P, d, d, d, d, i, P, P]),
+                "oc_run_trt": (i, [i, i, i, i, P, d, d, d, d, i, P, l]),
+                "oc_run_to_steady_trt": (i, [i, i, i, i, P, d, d, d, d, i, P, d, l, i, P, P]),
                 "oc_init": (i, [i, i, i, i, P, d, d, P]),
                 "oc_equilibrium": (i, [i, i, i, i, P, i, P, P, P, P, P]),
                 "oc_fields": (i, [i, i, i, i, P, P, P, P, P, P]),
@@ -126,22 +129,34 @@ def init(mask, rho_in: float, rho_out: float) -> np.ndarray:
     return f
 
 
-def step(mask, f, tau, rho_in, rho_out, eq=EQ_QUADRATIC) -> np.ndarray:
-    """One stream + boundary + collide step; returns the new post-collision state."""
+def tau_minus(tau: float, lam: float) -> float:
+    """TRT antisymmetric relaxation time for the magic parameter
+    Lambda = (tau - 1/2)(tau_minus - 1/2)."""
+    return 0.5 + lam / (tau - 0.5)
+
+
+def step(mask, f, tau, rho_in, rho_out, eq=EQ_QUADRATIC, tau_m=None) -> np.ndarray:
+    """One stream + boundary + collide step; returns the new post-collision state.
+    tau_m: TRT antisymmetric relaxation time (None = BGK)."""
     mask = _mask(mask)
     q, nx, ny, nz = _dims(mask)
     fin = np.ascontiguousarray(f, np.float64)
     out = np.zeros_like(fin)
-    if _get().oc_step(q, nx, ny, nz, _p(mask), tau, rho_in, rho_out, eq, _p(fin), _p(out)):
+    if tau_m is None:
+        rc = _get().oc_step(q, nx, ny, nz, _p(mask), tau, rho_in, rho_out, eq, _p(fin), _p(out))
+    else:
+        rc = _get().oc_step_trt(q, nx, ny, nz, _p(mask), tau, tau_m, rho_in, rho_out, eq, _p(fin), _p(out))
+    if rc:
         raise ValueError("bad arguments")
     return out
 
 
-def run(mask, f, tau, rho_in, rho_out, nsteps, eq=EQ_QUADRATIC) -> np.ndarray:
+def run(mask, f, tau, rho_in, rho_out, nsteps, eq=EQ_QUADRATIC, tau_m=None) -> np.ndarray:
     mask = _mask(mask)
     q, nx, ny, nz = _dims(mask)
     g = np.array(f, np.float64, copy=True, order="C")
-    if _get().oc_run(q, nx, ny, nz, _p(mask), tau, rho_in, rho_out, eq, _p(g), int(nsteps)):
+    if _get().oc_run_trt(q, nx, ny, nz, _p(mask), tau, 0.0 if tau_m is None else tau_m, rho_in, rho_out,
+                         eq, _p(g), int(nsteps)):
         raise ValueError("bad arguments")
     return g
 
@@ -194,7 +209,7 @@ def link_flux(mask, f) -> np.ndarray:
 
 
 def run_to_steady(mask, f, tau, rho_in, rho_out, tol, max_steps, interval=100,
-                  eq=EQ_QUADRATIC):
+                  eq=EQ_QUADRATIC, tau_m=None):
     """Iterate in place-copy; returns (f, status, steps, residual).
 
     status 0 = converged (r < tol), 1 = max_steps reached."""
@@ -203,8 +218,9 @@ def run_to_steady(mask, f, tau, rho_in, rho_out, tol, max_steps, interval=100,
     g = np.array(f, np.float64, copy=True, order="C")
     steps = C.c_long(0)
     res = C.c_double(0.0)
-    rc = _get().oc_run_to_steady(q, nx, ny, nz, _p(mask), tau, rho_in, rho_out, eq, _p(g),
-                                 tol, int(max_steps), int(interval), C.byref(steps), C.byref(res))
+    rc = _get().oc_run_to_steady_trt(q, nx, ny, nz, _p(mask), tau, 0.0 if tau_m is None else tau_m, rho_in,
+                                     rho_out, eq, _p(g), tol, int(max_steps), int(interval), C.byref(steps),
+                                     C.byref(res))
     if rc < 0:
         raise RuntimeError(f"oracle run_to_steady failed ({rc})")
     return g, rc, steps.value, res.value

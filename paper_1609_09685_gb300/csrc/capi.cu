@@ -453,6 +453,8 @@ void lbm_options_default(lbm_options* o) {
     o->strip_rows = 0;
     o->k_tol = 1e-5;
     o->in_place_pairs = 1;
+    o->collision = LBM_COLL_BGK;
+    o->trt_lambda = 3.0 / 16.0;
 }
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
@@ -512,7 +514,9 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     if (o.check_interval < 1 || o.stall_checks < 1 || !(o.rho_out > 0.0) || !(o.k_tol >= 0.0) ||
         (o.equilibrium != LBM_EQ_QUADRATIC && o.equilibrium != LBM_EQ_LINEAR) || o.block_threads < 0 ||
         o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255 ||
-        (o.in_place_pairs != 0 && o.in_place_pairs != 1))
+        (o.in_place_pairs != 0 && o.in_place_pairs != 1) ||
+        (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
+        !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     int q = force_q;
     if (!q) {
@@ -580,6 +584,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.seg_base = sb;
         G.nseg_dom = D.nseg;
         G.omega = (float)(1.0 / S.tau);
+        G.omega_m = o.collision == LBM_COLL_TRT ? (float)(1.0 / (0.5 + o.trt_lambda / (S.tau - 0.5))) : G.omega;
         G.drho_in = (float)S.drho;
         G.rho0 = (float)o.rho_out;
         G.active = 1;

@@ -65,7 +65,8 @@ struct DomainDev {
     int32_t nseg;        // segments per x-row, ceil(nx / 32)
     uint32_t seg_base;   // first global segment of the domain
     uint32_t nseg_dom;   // nseg * ny * nz
-    float omega;         // 1 / tau
+    float omega;         // 1 / tau (BGK; the even-part rate of TRT)
+    float omega_m;       // odd-part rate of TRT, 1 / tau_minus; equals omega for BGK
     float drho_in;       // rho_in - rho_0 (outlet carries rho_0 exactly)
     float rho0;          // rho_0 = rho_out
     int32_t active;      // 0 once retired by the steady-state control

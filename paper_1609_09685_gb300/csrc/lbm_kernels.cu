@@ -174,6 +174,24 @@ __device__ __forceinline__ void moments(const float (&f)[L::Q], float& dr, float
     }
 }
 
+// Post-collision values of the opposite pair (i, opp i) from the pair's even
+// and odd equilibrium terms sym = omega w (even part of f_eq - w rho_0) and
+// anti = omega_m 3 w (c_i . j).  BGK (omega_m == omega, warp-uniform per
+// domain): f* = (1 - omega) f + sym +- anti.  TRT (Ginzburg 2005): the even
+// part (f_i + f_o)/2 relaxes with omega, the odd part (f_i - f_o)/2 with
+// omega_m; hw = omega/2, hwm = omega_m/2.
+__device__ __forceinline__ void pair_relax(float fi, float fo, float sym, float anti, float omc, float hw,
+                                           float hwm, bool trt, float& oi, float& oo) {
+    if (!trt) {
+        oi = fmaf(omc, fi, sym + anti);
+        oo = fmaf(omc, fo, sym - anti);
+    } else {
+        const float hp = hw * (fi + fo), hm = hwm * (fi - fo);
+        oi = (fi - hp - hm) + (sym + anti);
+        oo = (fo - hp + hm) + (sym - anti);
+    }
+}
+
 template <int I, class L>
 struct Dir {
     static constexpr int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
@@ -300,10 +318,14 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     const bool zlo = (z == 0), zhi = (z == D.nz - 1);
     const bool xin = (x == 0), xout = (x == D.nx - 1);
     const bool edge = (it.w == 0) || ((int)it.w == D.nseg - 1);
-    // omega-scaled weights by |c|^2 class (0 rest, 1 axis, 2 diagonal) and 3x them
-    const float om = D.omega, omc = 1.0f - D.omega;
+    // omega-scaled weights by |c|^2 class (0 rest, 1 axis, 2 diagonal), and 3x
+    // the omega_m-scaled ones (the odd part's rate; omega_m = omega for BGK)
+    const float om = D.omega, omc = 1.0f - D.omega, omm = D.omega_m;
+    const bool trt = (omm != om);
+    const float hw = 0.5f * om, hwm = 0.5f * omm;
     const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
-    const float ow3[3] = {3.0f * ow[0], 3.0f * ow[1], 3.0f * ow[2]};
+    const float ow3[3] = {3.0f * (omm * (float)L::wd(0)), 3.0f * (omm * (float)L::wd(1)),
+                          3.0f * (omm * (float)L::wd(L::Q - 1))};
     float* const dst0 = A.dst[0];  // plane i starts at dst0 + i * PS
     constexpr int SL = stage_slots<L, OBS>();
     float* wbuf = smem + (size_t)wid * S * SL * 32;
@@ -421,7 +443,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             moments<L>(f, dr, jx, jy, jz);
             const float irho = __fdividef(1.0f, D.rho0 + dr);
             if (fl) {
-                // BGK by opposite pairs: f* = (1 - omega) f + omega w (a0 + 4.5 (c.j)^2/rho +- 3 c.j),
+                // BGK (or TRT) by opposite pairs: f* = (1 - omega) f + omega w (a0 + 4.5 (c.j)^2/rho +- 3 c.j),
                 // a0 = drho - 1.5 |j|^2 / rho (quadratic) or drho (linear).
                 const float jj = (L::D == 3) ? jx * jx + jy * jy + jz * jz : jx * jx + jy * jy;
                 const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jj, dr) : dr;
@@ -437,8 +459,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     const float cj = cdot<L>(i, jx, jy, jz);
                     const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
                     const float anti = ow3[cls] * cj;
-                    const float out_i = fmaf(omc, f[i], sym + anti);
-                    const float out_o = fmaf(omc, f[o], sym - anti);
+                    float out_i, out_o;
+                    pair_relax(f[i], f[o], sym, anti, omc, hw, hwm, trt, out_i, out_o);
                     dk[(uint32_t)i * PS] = out_i;
                     dk[(uint32_t)o * PS] = out_o;
                     dsum += (f[i] - out_i) + (f[o] - out_o);
@@ -537,7 +559,7 @@ namespace {
 // operations as the pull kernel, producing the Q post-collision values.
 template <class L, int EQ>
 __device__ __forceinline__ void relax(float (&f)[L::Q], bool edge, bool xin, bool xout, float drho_in, float rho0,
-                                      float om) {
+                                      float om, float omm) {
     constexpr int Q = L::Q;
     if (edge) {
         float g[Q];
@@ -553,8 +575,11 @@ __device__ __forceinline__ void relax(float (&f)[L::Q], bool edge, bool xin, boo
         for (int i = 0; i < Q; ++i) f[i] = xout ? g[i] : f[i];
     }
     const float omc = 1.0f - om;
+    const bool trt = (omm != om);
+    const float hw = 0.5f * om, hwm = 0.5f * omm;
     const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
-    const float ow3[3] = {3.0f * ow[0], 3.0f * ow[1], 3.0f * ow[2]};
+    const float ow3[3] = {3.0f * (omm * (float)L::wd(0)), 3.0f * (omm * (float)L::wd(1)),
+                          3.0f * (omm * (float)L::wd(L::Q - 1))};
     float dr, jx, jy, jz;
     moments<L>(f, dr, jx, jy, jz);
     const float irho = __fdividef(1.0f, rho0 + dr);
@@ -572,8 +597,7 @@ __device__ __forceinline__ void relax(float (&f)[L::Q], bool edge, bool xin, boo
         const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
         const float anti = ow3[cls] * cj;
         const float fi = f[i], fo = f[o];
-        f[i] = fmaf(omc, fi, sym + anti);
-        f[o] = fmaf(omc, fo, sym - anti);
+        pair_relax(fi, fo, sym, anti, omc, hw, hwm, trt, f[i], f[o]);
         dsum += (fi - f[i]) + (fo - f[o]);
     }
     f[0] = f0 + dsum;  // mass balance: see the pull kernel
@@ -684,7 +708,7 @@ __device__ __forceinline__ void aa_gather_body(const HotArgs& A) {
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega);
+            relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega, D.omega_m);
             if (fl[j]) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[e[j][opp<L>(i)]] = f[j][i];
@@ -794,7 +818,7 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
         }
 #pragma unroll
         for (int j = 0; j < RS; ++j) {
-            relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega);
+            relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega, D.omega_m);
             if ((flb >> j) & 1u) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[we[(j * Q + opp<L>(i)) * 32]] = f[j][i];
@@ -943,7 +967,7 @@ __device__ __forceinline__ void aa_gather_pipe_body(const HotArgs& A) {
             float f[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = sf[i * 32];
-            relax<L, EQ>(f, edge, xin, xout, D.drho_in, D.rho0, D.omega);
+            relax<L, EQ>(f, edge, xin, xout, D.drho_in, D.rho0, D.omega, D.omega_m);
             if (flq[st]) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[eq[st][opp<L>(i)]] = f[i];
@@ -1021,7 +1045,7 @@ __global__ void __launch_bounds__(256, LBM_AA_MINB_LOCAL) k_aa_local(const __gri
         float f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = v[i][n];
-        relax<L, EQ>(f, c != 0u, (c & 1u) != 0u, (c & 2u) != 0u, D.drho_in, D.rho0, D.omega);
+        relax<L, EQ>(f, c != 0u, (c & 1u) != 0u, (c & 2u) != 0u, D.drho_in, D.rho0, D.omega, D.omega_m);
 #pragma unroll
         for (int i = 0; i < Q; ++i) v[i][n] = f[i];
     }

@@ -30,6 +30,8 @@ LBM_ERR_INTERNAL = -7
 LBM_CANCELLED = -8
 LBM_EQ_QUADRATIC = 0
 LBM_EQ_LINEAR = 1
+LBM_COLL_BGK = 0
+LBM_COLL_TRT = 1
 NUM_OBS = 8
 
 # informational statuses that do not raise
@@ -57,6 +59,8 @@ class lbm_options(C.Structure):
         ("strip_rows", C.c_int32),
         ("k_tol", C.c_double),
         ("in_place_pairs", C.c_int32),
+        ("collision", C.c_int32),
+        ("trt_lambda", C.c_double),
     ]
 
 
@@ -166,7 +170,7 @@ def current_stream() -> Optional[int]:
 def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=200,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
-                 in_place_pairs=True) -> lbm_options:
+                 in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -181,6 +185,8 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.strip_rows = strip_rows
     o.k_tol = k_tol
     o.in_place_pairs = 1 if in_place_pairs else 0
+    o.collision = collision
+    o.trt_lambda = trt_lambda
     return o
 
 

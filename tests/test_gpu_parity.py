@@ -340,3 +340,67 @@ def test_cancel_flag_stops_the_run_between_intervals():
         flag.value = 0
         rc, st, steps, _ = lbm.lbm_run_to_steady(s, 1e-9, 100000)
         assert st[0] == lbm.LBM_OK
+
+
+# --------------------------------------------------------------------------
+# TRT collision
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lam", [3.0 / 16.0, 0.4])
+@pytest.mark.parametrize("pairs", [True, False])
+def test_trt_steps_match_oracle_2d_and_3d(lam, pairs):
+    """TRT on the GPU against the oracle's TRT: from the ramp start and from a
+    random state, 2D (all boundary kinds) and 3D, with in-place pairs and with
+    pull steps."""
+    rng = np.random.default_rng(41)
+    cases = [(9, _masks_2d()["8x6_corners"], lbm.lbm_create_domain),
+             (9, _masks_2d()["ragged70x13"], lbm.lbm_create_domain),
+             (19, _masks_3d()["ragged37x7x5"], lbm.lbm_create_domain_3d)]
+    tau, drho = 0.7, 1e-3
+    tm = O.tau_minus(tau, lam)
+    for q, mask, create in cases:
+        opts = lbm.make_options(collision=lbm.LBM_COLL_TRT, trt_lambda=lam, in_place_pairs=pairs)
+        with create(mask, tau, drho, opts) as s:
+            f0 = lbm.lbm_get_populations(s, 0)
+            lbm.lbm_step(s, 6)
+            _assert_close(lbm.lbm_get_populations(s, 0), O.run(mask, f0, tau, 1 + drho, 1.0, 6, tau_m=tm),
+                          q, mask)
+            f = _w(q) * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
+            f[mask.astype(bool)] = 0
+            lbm.lbm_set_populations(s, 0, f)
+            start = lbm.lbm_get_populations(s, 0)
+            lbm.lbm_step(s, 3)
+            _assert_close(lbm.lbm_get_populations(s, 0), O.run(mask, start, tau, 1 + drho, 1.0, 3, tau_m=tm),
+                          q, mask)
+
+
+def test_trt_channel_on_device_gives_lambda_permeability():
+    """Pressure-driven channel, linear equilibrium, TRT with Lambda = 3/16:
+    the mid-channel permeability is (h^2 - 1 + 8 Lambda)/12 for every tau."""
+    h, lam = 10, 3.0 / 16.0
+    ny, nx = h + 2, 6 * h
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    for tau in (0.6, 1.2):
+        opts = lbm.make_options(equilibrium=lbm.LBM_EQ_LINEAR, collision=lbm.LBM_COLL_TRT, trt_lambda=lam)
+        with lbm.lbm_create_domain(mask, tau, 1e-3, opts) as s:
+            lbm.lbm_run_to_steady(s, 1e-9, 400000)
+            rho, ux, _ = lbm.lbm_get_fields(s, 0)
+        xm = nx // 2
+        j = (rho * ux)[1:-1, xm]
+        beta = (rho[1:-1, xm + h // 2] - rho[1:-1, xm - h // 2]).mean() / (2 * (h // 2))
+        k_local = (tau - 0.5) / 3.0 * j.mean() / (-beta / 3.0)
+        assert k_local == pytest.approx((h * h - 1 + 8 * lam) / 12.0, rel=2e-4)
+
+
+def test_trt_converged_permeability_matches_oracle():
+    mask, _ = O.qsgs((40, 80), 9, 0.02, 0.72)
+    tau, drho, lam = 1.2, 1e-3, 3.0 / 16.0
+    opts = lbm.make_options(collision=lbm.LBM_COLL_TRT, trt_lambda=lam)
+    with lbm.lbm_create_domain(mask, tau, drho, opts) as s:
+        lbm.lbm_run_to_steady(s, 1e-9, 2_000_000)
+        k, _ = lbm.lbm_permeability(s)
+    f0 = O.init(mask, 1 + drho, 1.0)
+    g, rc, _, _ = O.run_to_steady(mask, f0, tau, 1 + drho, 1.0, 1e-10, 3_000_000, tau_m=O.tau_minus(tau, lam))
+    assert rc == 0
+    assert k[0] == pytest.approx(O.permeability(mask, g, tau, 1 + drho, 1.0), rel=1e-4)

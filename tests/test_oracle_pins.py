@@ -503,3 +503,89 @@ def test_mass_flow_rate_is_unique_with_boxed_in_boundary_node():
         jx6.append(rho[6, 0] * ux[6, 0])
     assert abs(jx6[1] - jx6[0]) > 1e-5          # the boxed-in node remembers its start
     assert ks[1] == pytest.approx(ks[0], rel=1e-5)  # the mass flow rate does not
+
+
+# ---------------------------------------------------------------------------
+# Two-relaxation-time collision (the multi-relaxation direction of Sec. 2)
+# ---------------------------------------------------------------------------
+
+def test_trt_with_equal_times_is_bgk():
+    """TRT relaxes the even and odd parts of f - f_eq separately; with
+    tau_minus = tau it must reproduce BGK (the two are separate code paths)."""
+    rng = np.random.default_rng(3)
+    for q, shape in ((9, (9, 17)), (19, (4, 5, 11))):
+        mask = (rng.random(shape) < 0.25).astype(np.uint8)
+        w = O.lattice(q)[1]
+        f = w * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
+        f[mask.astype(bool)] = 0
+        for eq in (O.EQ_QUADRATIC, O.EQ_LINEAR):
+            a = O.step(mask, f, 0.8, 1.001, 1.0, eq)
+            b = O.step(mask, f, 0.8, 1.001, 1.0, eq, tau_m=0.8)
+            assert np.abs(a - b).max() < 1e-15
+
+
+def test_trt_conserves_mass_and_keeps_the_rest_state():
+    """Collision invariants: in a closed box TRT conserves mass for any pair of
+    times, and the rest equilibrium stays a fixed point."""
+    rng = np.random.default_rng(5)
+    mask = np.zeros((10, 14), np.uint8)
+    mask[0] = mask[-1] = 1
+    mask[:, 0] = mask[:, -1] = 1
+    w = O.lattice(9)[1]
+    f = w * (1 + 0.05 * rng.standard_normal(mask.shape + (9,)))
+    f[mask.astype(bool)] = 0
+    g = O.run(mask, f, 0.7, 1.0, 1.0, 25, tau_m=1.9)
+    assert g.sum() == pytest.approx(f.sum(), rel=1e-13)
+    m1 = np.zeros((3, 5), np.uint8)
+    rest = O.init(m1, 1.0, 1.0)
+    out = O.run(m1, rest, 0.9, 1.0, 1.0, 10, tau_m=0.6)
+    assert np.abs(out - rest).max() < 1e-15
+
+
+@pytest.mark.parametrize("h", [8, 12])
+@pytest.mark.parametrize("tau", [0.6, 0.9, 1.5])
+def test_trt_channel_k_depends_only_on_lambda(h, tau):
+    """Pressure-driven channel with halfway bounce-back and the linear
+    equilibrium.  The BGK solution k = (h^2 - 1 + 8 (tau - 1/2)^2)/12 depends
+    on tau only through Lambda = (tau - 1/2)^2; TRT steady states depend on the
+    two times only through Lambda = (tau - 1/2)(tau_minus - 1/2), so TRT gives
+    k = (h^2 - 1 + 8 Lambda)/12 for every tau at fixed Lambda.  With the
+    'magic' Lambda = 3/16 the wall sits at the half link independently of the
+    viscosity."""
+    lam = 3.0 / 16.0
+    ny, nx = h + 2, 6 * h
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = mask[-1] = 1
+    drho = 1e-3
+    f = O.init(mask, 1 + drho, 1.0)
+    g, rc, steps, res = O.run_to_steady(mask, f, tau, 1 + drho, 1.0, 1e-12, 400000,
+                                        eq=O.EQ_LINEAR, tau_m=O.tau_minus(tau, lam))
+    assert rc == 0
+    rho, ux, _ = O.fields(mask, g)
+    xm = nx // 2
+    j = (rho * ux)[1:-1, xm]
+    beta = (rho[1:-1, xm + h // 2] - rho[1:-1, xm - h // 2]).mean() / (2 * (h // 2))
+    nu = (tau - 0.5) / 3.0
+    k_local = nu * j.mean() / (-beta / 3.0)
+    assert k_local == pytest.approx((h * h - 1 + 8 * lam) / 12.0, rel=1e-9)
+
+
+def test_trt_porous_k_is_viscosity_independent_at_fixed_lambda():
+    """On a porous QSGS domain the steady TRT permeability at fixed Lambda is
+    the same for every tau (Stokes regime, linear equilibrium), while BGK's
+    varies with tau."""
+    mask, _ = O.qsgs((16, 32), 5, 0.02, 0.72)
+    assert O.percolates(mask)
+    drho = 1e-4
+    ks, kb = [], []
+    for tau in (0.7, 1.3):
+        f = O.init(mask, 1 + drho, 1.0)
+        g, rc, _, _ = O.run_to_steady(mask, f, tau, 1 + drho, 1.0, 1e-9, 600000, eq=O.EQ_LINEAR,
+                                      tau_m=O.tau_minus(tau, 3.0 / 16.0))
+        assert rc == 0
+        ks.append(O.permeability(mask, g, tau, 1 + drho, 1.0))
+        g, rc, _, _ = O.run_to_steady(mask, f, tau, 1 + drho, 1.0, 1e-9, 600000, eq=O.EQ_LINEAR)
+        assert rc == 0
+        kb.append(O.permeability(mask, g, tau, 1 + drho, 1.0))
+    assert ks[0] == pytest.approx(ks[1], rel=1e-6)
+    assert abs(kb[0] - kb[1]) > 1e-3 * abs(kb[0])
