@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="sweep")
     p.add_argument("--interval", type=int, default=100)
+    p.add_argument("--collision", choices=["bgk", "trt"], default="bgk",
+                   help="BGK (the paper's model) or TRT with Lambda = 3/16")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -382,7 +384,8 @@ def run_native(args):
         masks.append(masks_cache[key])
     taus = [d.tau for d in wl.domains]
     drhos = [d.drho for d in wl.domains]
-    opts = lbm.make_options(stream=sp, check_interval=N)
+    coll = lbm.LBM_COLL_TRT if args.collision == "trt" else lbm.LBM_COLL_BGK
+    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll)
     s = lbm.lbm_batch_create(masks, taus, drhos, opts)
     fluid = s.fluid_nodes
     bytes_per_launch = 2 * 4 * q * fluid
@@ -493,6 +496,7 @@ def run_native(args):
             "data": "synthetic (seeded QSGS masks at the paper's sizes and porosities)",
             "config": {
                 "workload": wl.name, "domains": len(wl.domains), "lattice": f"D2Q9" if q == 9 else "D3Q19",
+                "collision": "TRT (Lambda = 3/16)" if args.collision == "trt" else "BGK",
                 "nodes": total_nodes, "fluid_nodes": fluid, "check_interval": N,
                 "step": f"{N - 1} fused stream-collide steps + 1 observing step + FP64 reduction + "
                         "host readback (one convergence-check interval)",
