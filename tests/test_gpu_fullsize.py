@@ -120,3 +120,33 @@ def test_converged_permeability_d3q19_small():
     g, rc, _, _ = O.run_to_steady(mask, O.init(mask, 1 + drho, 1.0), tau, 1 + drho, 1.0, 1e-10, 2_000_000)
     assert rc == 0
     assert k[0] == pytest.approx(O.permeability(mask, g, tau, 1 + drho, 1.0), rel=1e-4)
+
+
+def _golden_slow_domain():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "slow_domain_k.txt")
+    vals = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, v = line.split()
+            vals[key] = float(v)
+    return int(vals["steps"]), vals["k"]
+
+
+def test_slow_512x256_domain_keeps_k_within_1e4_of_fp64():
+    """A 512 x 256 QSGS domain whose slowest pressure mode relaxes over ~5e4
+    steps: after the same 250 000 steps from the same start, the GPU's FP32 k
+    is within 1e-4 of the FP64 oracle's (stored by
+    tests/golden/make_slow_domain_k.py).  With the rest population taken from
+    its own BGK formula instead of the mass balance, the FP32 rounding acts as
+    a fixed mass source at steady state and this domain's k settles 3.5e-4 off."""
+    steps, k_ref = _golden_slow_domain()
+    mask, _ = lbm.lbm_qsgs(1000006, (256, 512), 0.02, 0.621370254804748)
+    with lbm.lbm_create_domain(mask, 0.7653754091733804, 1e-3) as s:
+        for _ in range(steps // 1000 - 1):
+            lbm.lbm_step(s, 1000)
+        lbm.lbm_step(s, 999)
+        lbm.lbm_step_observe(s, 1)
+        assert lbm.lbm_get_step(s) == steps
+        k, _ = lbm.lbm_permeability(s)
+    assert k[0] == pytest.approx(k_ref, rel=1e-4)
