@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="sweep")
     p.add_argument("--interval", type=int, default=100)
+    p.add_argument("--local-kn", action="store_true",
+                   help="also time the local pore-size / local-Kn pass over every domain")
     p.add_argument("--collision", choices=["bgk", "trt"], default="bgk",
                    help="BGK (the paper's model) or TRT with Lambda = 3/16")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -464,6 +466,21 @@ def run_native(args):
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     (t_e2e,), (e2e_updates,) = combine_ranks(dist, "cuda", [t_e2e], [float(args.e2e_steps * N * fluid)])
+    lkn = None
+    if args.local_kn and rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kmax, kmean = [], []
+        for d in range(len(wl.domains)):
+            _, hh, kn = lbm.lbm_local_knudsen(s, d)
+            fl = kn > 0
+            kmax.append(float(kn[fl].max()) if fl.any() else 0.0)
+            kmean.append(float(kn[fl].mean()) if fl.any() else 0.0)
+        t_lkn = time.perf_counter() - t0
+        lkn = {"seconds_all_domains": t_lkn, "nodes": wl.cells,
+               "note": "lbm_local_knudsen per domain, host copies of d2, h and Kn included",
+               "max_local_kn_over_domain_kn": max(
+                   km / (np.sqrt(np.pi / 6) * (d.tau - 0.5) / d.nx) for km, d in zip(kmax, wl.domains))}
     s.close()
     ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
     ws = measure_warmstart(args, lbm, sp) if (args.warmstart and rank == 0) else None
@@ -527,6 +544,8 @@ def run_native(args):
             line["cpu_baseline"] = cpu
         if ttp is not None:
             line["time_to_permeability"] = ttp
+        if lkn is not None:
+            line["local_knudsen"] = lkn
         if ws is not None:
             line["warm_start"] = ws
         print(json.dumps(line), flush=True)

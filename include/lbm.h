@@ -187,6 +187,23 @@ lbm_status lbm_domain_fluid_nodes(lbm_handle h, int32_t d, int64_t* fluid_nodes)
 lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 
 /*
+ * Local pore size and local Knudsen number of domain d (Sec. 2 notes that the
+ * local Kn in narrow pores can be much larger than Kn = sqrt(pi/6)(tau-1/2)/N_x).
+ * The paper defines no pore size; here a fluid node's pore size is
+ * h = 2 D - 1, D the Euclidean distance in nodes to the nearest solid node of
+ * the domain (exact, integer D^2), so that the centre node of a channel of h
+ * fluid rows gets h; the local Kn is sqrt(pi/6)(tau - 1/2)/h.  The faces are
+ * not walls: a node that sees no solid node has D^2 = UINT32_MAX, h = +inf and
+ * Kn = 0.  Outputs are host arrays in the mask's dense layout (nz*ny*nx, x
+ * fastest), each nullable (at least one given): d2_out the squared distance
+ * (0 on solids), h_out the pore size and kn_out the local Kn (both 0 on
+ * solids).  Device scratch of 16 bytes per node comes from the solver's memory
+ * pool for the duration of the call; the call synchronises.
+ */
+lbm_status lbm_local_knudsen(lbm_handle h, int32_t d, uint32_t* d2_out, double* h_out, double* kn_out);
+
+/*
+ * Measurement: advance nsteps plain steps exactly as lbm_step does/*
  * Measurement: advance nsteps plain steps exactly as lbm_step does (same
  * kernels, same pairing), but launch every kernel on its own with a CUDA event
  * recorded before and after it on the solver's stream, instead of through the

@@ -32,7 +32,7 @@ __all__ = [
     "EQ_QUADRATIC", "EQ_LINEAR", "build", "lattice", "init", "step", "run",
     "equilibrium", "fields", "mean_jx", "permeability", "knudsen", "link_flux",
     "run_to_steady", "splitmix64", "qsgs_hash", "qsgs", "qsgs_grow_once", "percolates",
-    "Q_OF", "tau_minus",
+    "Q_OF", "tau_minus", "pore_d2", "local_knudsen",
 ]
 
 Q_OF = {2: 9, 3: 19}
@@ -76,6 +76,8 @@ def _get():
                 "oc_qsgs": (i, [i, i, i, u64, d, d, d, P]),
                 "oc_qsgs_grow_once": (i, [i, i, i, u64, u32, d, P, P]),
                 "oc_percolates": (i, [i, i, i, P]),
+                "oc_pore_d2": (i, [i, i, i, P, P]),
+                "oc_local_knudsen": (i, [i, i, i, P, d, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -264,3 +266,26 @@ def percolates(mask) -> bool:
     mask = _mask(mask)
     q, nx, ny, nz = _dims(mask)
     return bool(_get().oc_percolates(nx, ny, nz, _p(mask)))
+
+
+def pore_d2(mask) -> np.ndarray:
+    """Squared distance (nodes) from each node to the nearest solid node; 0 on
+    solids, 2**32 - 1 where the domain has no solid."""
+    mask = _mask(mask)
+    _, nx, ny, nz = _dims(mask)
+    out = np.zeros(mask.shape, np.uint32)
+    if _get().oc_pore_d2(nx, ny, nz, _p(mask), _p(out)):
+        raise ValueError("bad arguments")
+    return out
+
+
+def local_knudsen(mask, tau):
+    """(h, Kn): local pore size 2 D - 1 and local Knudsen number
+    sqrt(pi/6)(tau - 1/2)/h on fluid nodes, 0 on solids."""
+    mask = _mask(mask)
+    _, nx, ny, nz = _dims(mask)
+    h = np.zeros(mask.shape, np.float64)
+    kn = np.zeros(mask.shape, np.float64)
+    if _get().oc_local_knudsen(nx, ny, nz, _p(mask), tau, _p(h), _p(kn)):
+        raise ValueError("bad arguments")
+    return h, kn

@@ -764,6 +764,37 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
     return s;
 }
 
+lbm_status lbm_local_knudsen(lbm_handle h, int32_t d, uint32_t* d2_out, double* h_out, double* kn_out) {
+    lbm_status s = check_domain(h, d);
+    if (s != LBM_OK) return s;
+    if (!d2_out && !h_out && !kn_out) return fail(h, LBM_ERR_ARG, "no output requested");
+    const DomainHost& D = h->dom[d];
+    const uint64_t total = (uint64_t)D.nx * D.ny * D.nz;
+    const uint8_t* mask = h->d_mask + D.mask_base;
+    uint32_t *d2 = nullptr, *tmp = nullptr;
+    double* dev = nullptr;  // h then kn, total doubles each
+    auto release = [&]() {
+        if (d2) cudaFreeAsync(d2, h->st);
+        if (tmp) cudaFreeAsync(tmp, h->st);
+        if (dev) cudaFreeAsync(dev, h->st);
+    };
+    cudaError_t e = dmalloc(h, &d2, sizeof(uint32_t) * total);
+    if (e == cudaSuccess) e = dmalloc(h, &tmp, sizeof(uint32_t) * total);
+    if (e == cudaSuccess) e = dmalloc(h, &dev, sizeof(double) * 2 * total);
+    if (e == cudaSuccess) e = launch_pore_d2(mask, D.nx, D.ny, D.nz, d2, tmp, h->st);
+    if (e == cudaSuccess) e = launch_local_kn(mask, d2, total, D.tau, dev, dev + total, h->st);
+    if (e == cudaSuccess && d2_out)
+        e = cudaMemcpyAsync(d2_out, d2, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h_out)
+        e = cudaMemcpyAsync(h_out, dev, sizeof(double) * total, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && kn_out)
+        e = cudaMemcpyAsync(kn_out, dev + total, sizeof(double) * total, cudaMemcpyDeviceToHost, h->st);
+    release();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_local_knudsen");
+    return LBM_OK;
+}
+
 lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int64_t* counts) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (nsteps < 0 || nsteps > 100000) return fail(h, LBM_ERR_ARG, "nsteps must be in [0, 100000]");

@@ -63,6 +63,13 @@ int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double p
                   double d_face, uint8_t* d_mask, const QsgsScratch& sc, cudaStream_t st,
                   int* iterations, cudaError_t* cuda_err);
 
+// Local pore size (pore.cu): exact squared distance to the nearest solid node of
+// a dense mask (d2, tmp: nx*ny*nz uint32 each), then h = 2 D - 1 and the local Kn.
+cudaError_t launch_pore_d2(const uint8_t* mask, int nx, int ny, int nz, uint32_t* d2, uint32_t* tmp,
+                           cudaStream_t st);
+cudaError_t launch_local_kn(const uint8_t* mask, const uint32_t* d2, uint64_t total, double tau, double* h_out,
+                            double* kn_out, cudaStream_t st);
+
 // Record the detail string lbm_last_error(NULL) returns on this thread (capi.cu).
 void set_thread_error(const std::string& msg);
 

@@ -109,6 +109,7 @@ def load(path: Optional[str] = None):
         "lbm_step": (i32, [P, i64]),
         "lbm_step_observe": (i32, [P, i64, P]),
         "lbm_profile_steps": (i32, [P, i64, P, P]),
+        "lbm_local_knudsen": (i32, [P, i32, P, P, P]),
         "lbm_run_to_steady": (i32, [P, d, i64, P, P, P]),
         "lbm_permeability": (i32, [P, P, P]),
         "lbm_get_fields": (i32, [P, i32, P, P, P, P]),
@@ -318,6 +319,18 @@ def lbm_step_observe(s: Solver, nsteps: int) -> np.ndarray:
     out = np.zeros((s.n_domains, NUM_OBS), np.float64)
     _check(load().lbm_step_observe(s.handle, int(nsteps), _ptr(out)), s.handle)
     return out
+
+
+def lbm_local_knudsen(s: Solver, d: int):
+    """(d2, h, kn) of domain d in the mask's shape: squared distance to the
+    nearest solid node, local pore size 2 D - 1 and local Knudsen number."""
+    shape = s.masks[d].shape
+    n_nodes = int(np.prod(shape))
+    d2 = np.zeros(n_nodes, np.uint32)
+    h = np.zeros(n_nodes, np.float64)
+    kn = np.zeros(n_nodes, np.float64)
+    _check(load().lbm_local_knudsen(s.handle, int(d), _ptr(d2), _ptr(h), _ptr(kn)), s.handle)
+    return d2.reshape(shape), h.reshape(shape), kn.reshape(shape)
 
 
 KERNEL_KINDS = ("gather", "local", "pull", "pull_observe")

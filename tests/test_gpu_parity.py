@@ -404,3 +404,28 @@ def test_trt_converged_permeability_matches_oracle():
     g, rc, _, _ = O.run_to_steady(mask, f0, tau, 1 + drho, 1.0, 1e-10, 3_000_000, tau_m=O.tau_minus(tau, lam))
     assert rc == 0
     assert k[0] == pytest.approx(O.permeability(mask, g, tau, 1 + drho, 1.0), rel=1e-4)
+
+
+# --------------------------------------------------------------------------
+# Local pore size and local Knudsen number
+# --------------------------------------------------------------------------
+
+def test_local_knudsen_matches_oracle_bit_exact():
+    """Integer squared distances bit-exact with the oracle's brute force, on 2D
+    and 3D masks spanning many blocks, a channel and a mask without solids."""
+    rng = np.random.default_rng(51)
+    cases = [(O.qsgs((70, 150), 3, 0.02, 0.7)[0], 0.8, lbm.lbm_create_domain),
+             ((rng.random((7, 13, 33)) < 0.2).astype(np.uint8), 0.9, lbm.lbm_create_domain_3d)]
+    ch = np.zeros((9, 40), np.uint8)
+    ch[0] = ch[-1] = 1
+    cases.append((ch, 0.7, lbm.lbm_create_domain))
+    cases.append((np.zeros((5, 12), np.uint8), 0.7, lbm.lbm_create_domain))
+    for mask, tau, create in cases:
+        with create(mask, tau, 1e-3) as s:
+            d2, h, kn = lbm.lbm_local_knudsen(s, 0)
+        assert np.array_equal(d2, O.pore_d2(mask))
+        h_o, kn_o = O.local_knudsen(mask, tau)
+        assert np.array_equal(np.isinf(h), np.isinf(h_o))
+        fin = np.isfinite(h_o)
+        assert np.allclose(h[fin], h_o[fin], rtol=0, atol=1e-12)
+        assert np.allclose(kn, kn_o, rtol=1e-14, atol=0)

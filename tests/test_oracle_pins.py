@@ -589,3 +589,56 @@ def test_trt_porous_k_is_viscosity_independent_at_fixed_lambda():
         kb.append(O.permeability(mask, g, tau, 1 + drho, 1.0))
     assert ks[0] == pytest.approx(ks[1], rel=1e-6)
     assert abs(kb[0] - kb[1]) > 1e-3 * abs(kb[0])
+
+
+# ---------------------------------------------------------------------------
+# Local pore size and local Knudsen number (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def test_pore_distance_closed_forms():
+    # 3-4-5: one solid node; the fluid node 3 along x and 4 along y is 5 away
+    m = np.zeros((6, 8), np.uint8)
+    m[0, 0] = 1
+    d2 = O.pore_d2(m)
+    assert d2[4, 3] == 25 and d2[0, 0] == 0 and d2[0, 1] == 1 and d2[1, 1] == 2
+    assert d2[5, 7] == 5 * 5 + 7 * 7
+    # no solid anywhere: infinite distance, zero local Kn
+    e = np.zeros((3, 4), np.uint8)
+    assert np.all(O.pore_d2(e) == np.uint32(2**32 - 1))
+    h, kn = O.local_knudsen(e, 0.8)
+    assert np.all(np.isinf(h)) and np.all(kn == 0)
+    # 3D: the nearest solid of a corner node along the space diagonal
+    c = np.zeros((4, 4, 4), np.uint8)
+    c[3, 3, 3] = 1
+    assert O.pore_d2(c)[0, 0, 0] == 27
+
+
+@pytest.mark.parametrize("h", [1, 4, 7])
+def test_channel_pore_size_and_local_kn(h):
+    """Channel of h fluid rows between solid rows: the centre row's pore size
+    is h (odd h) and its local Kn is sqrt(pi/6)(tau - 1/2)/h; every row's pore
+    size is 2 (distance to the nearer wall) - 1."""
+    tau = 0.9
+    m = np.zeros((h + 2, 10), np.uint8)
+    m[0] = m[-1] = 1
+    hh, kn = O.local_knudsen(m, tau)
+    for r in range(1, h + 1):
+        dwall = min(r, h + 1 - r)
+        assert np.all(hh[r] == 2 * dwall - 1)
+    c = (h + 1) // 2
+    if h % 2 == 1:
+        assert np.all(hh[c] == h)
+        assert np.allclose(kn[c], np.sqrt(np.pi / 6) * (tau - 0.5) / h, rtol=1e-15)
+    assert np.all(hh[0] == 0) and np.all(kn[-1] == 0)
+
+
+def test_pore_distance_is_the_minimum_over_solid_nodes():
+    """Independent numpy restatement on a random mask: for every fluid node the
+    squared distance equals the minimum over all solid nodes."""
+    rng = np.random.default_rng(13)
+    m = (rng.random((5, 7, 9)) < 0.15).astype(np.uint8)
+    d2 = O.pore_d2(m)
+    zs, ys, xs = np.nonzero(m)
+    for (z, y, x) in zip(*np.nonzero(m == 0)):
+        ref = ((zs - z) ** 2 + (ys - y) ** 2 + (xs - x) ** 2).min()
+        assert d2[z, y, x] == ref
