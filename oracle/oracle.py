@@ -32,7 +32,8 @@ __all__ = [
     "EQ_QUADRATIC", "EQ_LINEAR", "build", "lattice", "init", "step", "run",
     "equilibrium", "fields", "mean_jx", "permeability", "knudsen", "link_flux",
     "run_to_steady", "splitmix64", "qsgs_hash", "qsgs", "qsgs_grow_once", "percolates",
-    "Q_OF", "tau_minus", "pore_d2", "local_knudsen",
+    "Q_OF", "tau_minus", "pore_d2", "local_knudsen", "step_forced", "run_forced",
+    "permeability_forced", "run_forced_to_steady",
 ]
 
 Q_OF = {2: 9, 3: 19}
@@ -77,6 +78,9 @@ def _get():
                 "oc_qsgs_grow_once": (i, [i, i, i, u64, u32, d, P, P]),
                 "oc_percolates": (i, [i, i, i, P]),
                 "oc_pore_d2": (i, [i, i, i, P, P]),
+                "oc_step_forced": (i, [i, i, i, i, P, d, d, i, P, P]),
+                "oc_run_forced": (i, [i, i, i, i, P, d, d, i, P, l]),
+                "oc_permeability_forced": (d, [i, i, i, i, P, P, d, d, d]),
                 "oc_local_knudsen": (i, [i, i, i, P, d, P, P]),
             }
             for name, (res, args) in sig.items():
@@ -289,3 +293,52 @@ def local_knudsen(mask, tau):
     if _get().oc_local_knudsen(nx, ny, nz, _p(mask), tau, _p(h), _p(kn)):
         raise ValueError("bad arguments")
     return h, kn
+
+
+def step_forced(mask, f, tau, g, eq=EQ_QUADRATIC) -> np.ndarray:
+    """One step of force-driven flow with every face periodic (body
+    acceleration g along +x, Guo forcing)."""
+    mask = _mask(mask)
+    q, nx, ny, nz = _dims(mask)
+    fin = np.ascontiguousarray(f, np.float64)
+    out = np.zeros_like(fin)
+    if _get().oc_step_forced(q, nx, ny, nz, _p(mask), tau, g, eq, _p(fin), _p(out)):
+        raise ValueError("bad arguments")
+    return out
+
+
+def run_forced(mask, f, tau, g, nsteps, eq=EQ_QUADRATIC) -> np.ndarray:
+    mask = _mask(mask)
+    q, nx, ny, nz = _dims(mask)
+    h = np.array(f, np.float64, copy=True, order="C")
+    if _get().oc_run_forced(q, nx, ny, nz, _p(mask), tau, g, eq, _p(h), int(nsteps)):
+        raise ValueError("bad arguments")
+    return h
+
+
+def permeability_forced(mask, f, tau, g, rho0=1.0) -> float:
+    """Eq. (2): k = nu <u>/g over all grid nodes."""
+    mask = _mask(mask)
+    q, nx, ny, nz = _dims(mask)
+    return _get().oc_permeability_forced(q, nx, ny, nz, _p(mask), _p(np.ascontiguousarray(f, np.float64)),
+                                         tau, g, rho0)
+
+
+def run_forced_to_steady(mask, f, tau, g, tol, max_steps, interval=100, eq=EQ_QUADRATIC):
+    """Steps in intervals until the relative velocity change over an interval
+    is below tol; returns (f, status, steps, residual), status 0 = converged."""
+    mask = _mask(mask)
+    h = np.array(f, np.float64, copy=True, order="C")
+    fl = ~mask.astype(bool)
+    prev = np.stack(fields(mask, h)[1:], axis=-1)[fl]
+    steps, r = 0, np.inf
+    while steps < max_steps:
+        h = run_forced(mask, h, tau, g, interval, eq)
+        steps += interval
+        cur = np.stack(fields(mask, h)[1:], axis=-1)[fl]
+        den = np.sqrt((cur ** 2).sum())
+        r = np.sqrt(((cur - prev) ** 2).sum()) / den if den > 0 else np.inf
+        prev = cur
+        if r < tol:
+            return h, 0, steps, r
+    return h, 1, steps, r

@@ -642,3 +642,73 @@ def test_pore_distance_is_the_minimum_over_solid_nodes():
     for (z, y, x) in zip(*np.nonzero(m == 0)):
         ref = ((zs - z) ** 2 + (ys - y) ** 2 + (xs - x) ** 2).min()
         assert d2[z, y, x] == ref
+
+
+# ---------------------------------------------------------------------------
+# Force-driven periodic flow: the 3D experiment of Sec. 2 (Eq. 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eq", [0, 1])
+def test_forced_all_fluid_box_gains_exactly_F_per_step(eq):
+    """Fully periodic, no solid: the Guo forcing adds exactly F = rho_0 g to
+    each node's post-collision momentum per step, and the flow stays uniform;
+    mass is conserved."""
+    m = np.zeros((4, 5), np.uint8)
+    f = O.init(m, 1.0, 1.0)
+    g = 1e-5
+    for t in range(1, 4):
+        f = O.run_forced(m, f, 0.8, g, 1, eq)
+        rho, ux, uy = O.fields(m, f)
+        assert (rho * ux).sum() == pytest.approx(t * m.size * g, rel=1e-12)
+        assert np.ptp(ux) == 0 and np.abs(uy).max() < 1e-15
+        assert rho.sum() == pytest.approx(m.size, rel=1e-14)
+
+
+def test_forced_channel_slip_is_width_independent():
+    """Between two bounce-back walls the bulk momentum balance makes the
+    steady profile a parabola of curvature -g/nu, so the wall correction is
+    the same for every width: k(h2) - k(h1) = (h2^2 - h1^2)/12 exactly, for
+    each tau, with either equilibrium."""
+    g = 1e-6
+    for eq in (0, 1):
+        for tau in (0.7, 1.2):
+            ks = []
+            for h in (6, 10):
+                m = np.zeros((h + 2, 4), np.uint8)
+                m[0] = m[-1] = 1
+                f, rc, _, _ = O.run_forced_to_steady(m, O.init(m, 1.0, 1.0), tau, g, 1e-13, 400000, eq=eq)
+                assert rc == 0
+                ks.append(O.permeability_forced(m, f, tau, g) * (h + 2) / h)
+            assert ks[1] - ks[0] == pytest.approx((100 - 36) / 12.0, rel=1e-9)
+
+
+def test_forced_plates_3d_equal_the_2d_channel():
+    """D3Q19 between two walls, periodic in x and z: the flow is z-invariant
+    and D3Q19 projects onto the D2Q9 weights, so k equals the D2Q9 channel's."""
+    h, tau, g = 6, 0.9, 1e-6
+    m2 = np.zeros((h + 2, 4), np.uint8)
+    m2[0] = m2[-1] = 1
+    m3 = np.zeros((3, h + 2, 4), np.uint8)
+    m3[:, 0] = m3[:, -1] = 1
+    f2, rc2, _, _ = O.run_forced_to_steady(m2, O.init(m2, 1.0, 1.0), tau, g, 1e-11, 400000)
+    f3, rc3, _, _ = O.run_forced_to_steady(m3, O.init(m3, 1.0, 1.0), tau, g, 1e-11, 400000)
+    assert rc2 == 0 and rc3 == 0
+    assert O.permeability_forced(m3, f3, tau, g) == pytest.approx(O.permeability_forced(m2, f2, tau, g),
+                                                                 rel=1e-9)
+
+
+def test_forced_k_is_force_independent_only_with_the_stokes_equilibrium():
+    """Sec. 2's 3D finding (Fig. 5): with the linear (Stokes) equilibrium and
+    a constant force density the whole update is linear in (f, g), so
+    k = nu <u>/g does not depend on g; with the quadratic equilibrium inertia
+    makes it depend on g."""
+    mask, _ = O.qsgs((8, 10, 12), 4, 0.05, 0.75)
+    tau = 0.8
+    k = {}
+    for eq in (0, 1):
+        for g in (1e-6, 5e-4):
+            f, rc, _, _ = O.run_forced_to_steady(mask, O.init(mask, 1.0, 1.0), tau, g, 1e-10, 100000, eq=eq)
+            assert rc == 0
+            k[eq, g] = O.permeability_forced(mask, f, tau, g)
+    assert k[1, 1e-6] == pytest.approx(k[1, 5e-4], rel=1e-9)
+    assert abs(k[0, 5e-4] - k[0, 1e-6]) > 1e-6 * abs(k[0, 1e-6])
