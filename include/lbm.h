@@ -165,6 +165,22 @@ lbm_status lbm_qsgs_noalloc(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, d
  */
 lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt,
                             lbm_handle* out);
+
+/*
+ * Force-driven flow with every face periodic: the paper's 3D experiment
+ * (Sec. 2, Eq. 2).  n domains as in lbm_batch_create (descs[d].drho is
+ * ignored), each driven by a body acceleration g[d] along +x (host array of n
+ * doubles) instead of the pressure boundaries.  Solids bounce back half way;
+ * the forcing is Guo, Zheng & Shi (2002) with force density F = rho_out g;
+ * lbm_permeability then returns Eq. 2's k = nu <u>/g, <u> the sum over fluid
+ * nodes of rho u_x over rho_out N_grid (rho u_x of the stored post-collision
+ * state plus F/2).  BGK only (opt->collision must be LBM_COLL_BGK); steps are
+ * pull steps of a kernel of their own (opt->in_place_pairs is ignored).
+ * lbm_save, lbm_nn_targets and lbm_warm_start return LBM_ERR_ARG on such a
+ * solver.
+ */
+lbm_status lbm_batch_create_forced(int32_t n, const lbm_domain_desc* descs, const double* g,
+                                   const lbm_options* opt, lbm_handle* out);
 /* Single 2D (D2Q9) domain: a batch of one. */
 lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, double tau,
                              double drho, const lbm_options* opt, lbm_handle* out);

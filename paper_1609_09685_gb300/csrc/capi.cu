@@ -32,6 +32,7 @@ thread_local std::string t_err;
 struct DomainHost {
     int32_t nx = 0, ny = 0, nz = 1;
     double tau = 1.0, drho = 0.0;
+    double g = 0.0;           // body acceleration along +x (force-driven solvers)
     uint32_t seg_begin = 0, nseg = 0;
     uint32_t fluid_begin = 0, fluid_count = 0;
     uint64_t mask_base = 0;
@@ -86,6 +87,8 @@ struct lbm_solver {
     uint2* d_vitems = nullptr;  // local-step work items
     uint32_t nvitems = 0;
     uint32_t* d_face = nullptr;  // inlet/outlet bits per compact slot
+    bool forced = false;         // force-driven, every face periodic (lbm_batch_create_forced)
+    float* d_gforce = nullptr;   // body acceleration per domain (force-driven solvers)
     uint32_t nitems = 0;
     uint8_t* d_mask = nullptr;
     uint32_t nseg_total = 0;
@@ -216,6 +219,7 @@ void free_solver(lbm_handle h) {
         dfree(h, h->d_uprev);
         dfree(h, h->d_partials);
         dfree(h, h->d_obs);
+        dfree(h, h->d_gforce);
     }
     if (h->h_obs) cudaFreeHost(h->h_obs);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
@@ -229,8 +233,11 @@ double knudsen(double tau, int nx) { return std::sqrt(M_PI / 6.0) * (tau - 0.5) 
 // planes; its plane average <J> = sum_link / (N_x - 1) is the mass flow rate,
 // U = <J> / (rho A) with A = N_y N_z, mu = rho nu, nu = (tau - 1/2)/3 (Eq. 1),
 // dP = c_s^2 drho over L = N_x - 1:  k = nu <J> (N_x - 1) / (A c_s^2 drho).
-double darcy_k(const DomainHost& D, double sum_link) {
+// Force-driven solvers (Eq. 2): k = nu <u> / g, <u> the sum over fluid nodes of
+// rho u_x (observable 0) over rho_0 N_grid.
+double darcy_k(const DomainHost& D, double sum_link, bool forced, double rho0) {
     const double nu = (D.tau - 0.5) / 3.0;
+    if (forced) return nu * sum_link / (rho0 * (double)D.nx * D.ny * D.nz) / D.g;
     const double jmean = sum_link / (double)(D.nx - 1);
     return nu * jmean * (double)(D.nx - 1) / ((double)D.ny * D.nz * (1.0 / 3.0) * D.drho);
 }
@@ -277,7 +284,20 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     const HotArgs A = h->hot();
     const int64_t o = (obs && n > 0) ? 1 : 0;
     int64_t plain = n - o;
-    if (h->opt.in_place_pairs) {
+    if (h->forced) {
+        for (int64_t k = 0; k < n; ++k) {
+            const bool ob = (o == 1) && (k == n - 1);
+            if (prof) CK(h, prof->mark(h->st));
+            CK(h, launch_periodic_step(h->q, h->eq, ob, A, h->d_gforce, h->d_g[h->cur], h->d_g[h->cur ^ 1],
+                                       h->d_uprev, h->d_partials, h->st));
+            if (prof) {
+                CK(h, prof->mark(h->st));
+                prof->kind.push_back(ob ? 3 : 2);
+            }
+            h->cur ^= 1;
+        }
+        plain = 0;
+    } else if (h->opt.in_place_pairs) {
         for (; plain >= 2; plain -= 2) {
             if (!prof) {
                 CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->st));
@@ -291,7 +311,7 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
             }
         }
     }
-    for (int64_t k = 0; k < plain + o; ++k) {
+    for (int64_t k = 0; k < (h->forced ? 0 : plain + o); ++k) {
         const bool ob = (o == 1) && (k == plain);
         if (prof) CK(h, prof->mark(h->st));
         CK(h, launch_stream_collide(h->q, h->eq, ob, A, h->d_g[h->cur], h->d_g[h->cur ^ 1], h->d_uprev,
@@ -500,7 +520,7 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
 }
 
 static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, int force_q,
-                              lbm_handle* out) {
+                              lbm_handle* out, const double* gforce = nullptr) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
     *out = nullptr;
     if (n < 1 || !descs) return fail(nullptr, LBM_ERR_ARG, "need at least one domain");
@@ -518,6 +538,12 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
         !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
+    if (gforce) {
+        if (o.collision != LBM_COLL_BGK) return fail(nullptr, LBM_ERR_ARG, "force-driven solvers use BGK");
+        o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
+        for (int d = 0; d < n; ++d)
+            if (!std::isfinite(gforce[d])) return fail(nullptr, LBM_ERR_ARG, "g must be finite");
+    }
     int q = force_q;
     if (!q) {
         q = 9;
@@ -532,7 +558,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         if (D.ny > 65535 || D.nz > 65535) return fail(nullptr, LBM_ERR_ARG, "ny and nz must be <= 65535");
         if (q == 9 && D.nz != 1) return fail(nullptr, LBM_ERR_ARG, "D2Q9 domains need nz = 1");
         if (!(D.tau > 0.5) || !std::isfinite(D.tau)) return fail(nullptr, LBM_ERR_ARG, "tau must be > 0.5");
-        if (!std::isfinite(D.drho) || std::fabs(D.drho) >= o.rho_out)
+        if (!gforce && (!std::isfinite(D.drho) || std::fabs(D.drho) >= o.rho_out))
             return fail(nullptr, LBM_ERR_ARG, "drho must be finite and |drho| < rho_out");
         const uint64_t N = (uint64_t)D.nx * D.ny * D.nz;
         uint8_t bad = 0;  // OR of the bits above bit 0 (a branch-free loop the compiler vectorises)
@@ -547,6 +573,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     lbm_handle h = new lbm_solver();
     h->q = q;
     h->eq = o.equilibrium;
+    h->forced = gforce != nullptr;
     h->opt = o;
     if (o.stream) {
         h->st = (cudaStream_t)o.stream;
@@ -571,7 +598,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         D.ny = S.ny;
         D.nz = S.nz;
         D.tau = S.tau;
-        D.drho = S.drho;
+        D.drho = gforce ? 0.0 : S.drho;
+        D.g = gforce ? gforce[d] : 0.0;
         D.seg_begin = sb;
         D.nseg = (uint32_t)((S.nx + kSegW - 1) / kSegW) * S.ny * S.nz;
         D.mask_base = mb;
@@ -585,7 +613,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.nseg_dom = D.nseg;
         G.omega = (float)(1.0 / S.tau);
         G.omega_m = o.collision == LBM_COLL_TRT ? (float)(1.0 / (0.5 + o.trt_lambda / (S.tau - 0.5))) : G.omega;
-        G.drho_in = (float)S.drho;
+        G.drho_in = gforce ? 0.0f : (float)S.drho;
         G.rho0 = (float)o.rho_out;
         G.active = 1;
         G.mask_base = mb;
@@ -705,6 +733,13 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(dmalloc(h, &h->d_uprev, sizeof(float) * D * h->pstride));
     CKC(dmalloc(h, &h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
     CKC(dmalloc(h, &h->d_obs, sizeof(double) * kNumObs * n));
+    if (gforce) {
+        std::vector<float> gf(n);
+        for (int d = 0; d < n; ++d) gf[d] = (float)gforce[d];
+        CKC(dmalloc(h, &h->d_gforce, sizeof(float) * n));
+        CKC(cudaMemcpyAsync(h->d_gforce, gf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st));
+        CKC(cudaStreamSynchronize(h->st));
+    }
     CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
     CKC(cudaMemsetAsync(h->d_g[0], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));
@@ -716,6 +751,12 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
 
 lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, lbm_handle* out) {
     return create_impl(n, descs, opt, 0, out);
+}
+
+lbm_status lbm_batch_create_forced(int32_t n, const lbm_domain_desc* descs, const double* g, const lbm_options* opt,
+                                   lbm_handle* out) {
+    if (!g) return fail(nullptr, LBM_ERR_ARG, "g is null");
+    return create_impl(n, descs, opt, 0, out, g);
 }
 
 lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, double tau, double drho,
@@ -881,7 +922,8 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
             else r = (o[1] == 0.0) ? 0.0 : INFINITY;
             D.residual = r;
             D.h_step.push_back(h->step);
-            D.h_k.push_back(D.drho != 0.0 ? darcy_k(D, o[0]) : NAN);
+            D.h_k.push_back((h->forced ? D.g != 0.0 : D.drho != 0.0) ? darcy_k(D, o[0], h->forced, h->opt.rho_out)
+                                                                     : NAN);
             D.h_r.push_back(r);
             D.h_t.push_back(std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
             lbm_status ds = LBM_NOT_CONVERGED;
@@ -958,11 +1000,11 @@ lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
     lbm_status rs = LBM_OK;
     for (size_t d = 0; d < h->dom.size(); ++d) {
         const DomainHost& D = h->dom[d];
-        if (D.drho == 0.0) {
+        if (h->forced ? D.g == 0.0 : D.drho == 0.0) {
             k[d] = NAN;
-            rs = fail(h, LBM_ERR_ARG, "drho = 0: permeability undefined");
+            rs = fail(h, LBM_ERR_ARG, h->forced ? "g = 0: permeability undefined" : "drho = 0: permeability undefined");
         } else {
-            k[d] = darcy_k(D, D.obs[0]);
+            k[d] = darcy_k(D, D.obs[0], h->forced, h->opt.rho_out);
         }
         if (kn) kn[d] = knudsen(D.tau, D.nx);
     }
@@ -1084,6 +1126,7 @@ lbm_status lbm_nn_targets(lbm_handle h, int32_t d, float* out_dev) {
     lbm_status s = check_domain(h, d);
     if (s != LBM_OK) return s;
     if (!out_dev) return fail(h, LBM_ERR_ARG, "null output");
+    if (h->forced) return fail(h, LBM_ERR_ARG, "targets are defined for pressure-driven domains");
     if (h->q != 9) return fail(h, LBM_ERR_ARG, "warm-start targets are defined for 2D (D2Q9) domains");
     const DomainHost& D = h->dom[d];
     if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: targets undefined");
@@ -1096,6 +1139,7 @@ lbm_status lbm_warm_start(lbm_handle h, int32_t d, const void* pred_dev, int32_t
     lbm_status s = check_domain(h, d);
     if (s != LBM_OK) return s;
     if (!pred_dev || ld < 3) return fail(h, LBM_ERR_ARG, "need a prediction with at least 3 channels");
+    if (h->forced) return fail(h, LBM_ERR_ARG, "the warm start is defined for pressure-driven domains");
     if (h->q != 9) return fail(h, LBM_ERR_ARG, "the warm start is defined for 2D (D2Q9) domains");
     DomainHost& D = h->dom[d];
     if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: nothing to predict");
@@ -1118,6 +1162,7 @@ static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
 
 lbm_status lbm_save(lbm_handle h, const char* path) {
     if (!h || !path) return fail(h, LBM_ERR_ARG, "null argument");
+    if (h->forced) return fail(h, LBM_ERR_ARG, "checkpoints hold pressure-driven solvers only");
     CK(h, cudaStreamSynchronize(h->st));
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(h, LBM_ERR_IO, std::string("cannot open ") + path);

@@ -63,6 +63,11 @@ int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double p
                   double d_face, uint8_t* d_mask, const QsgsScratch& sc, cudaStream_t st,
                   int* iterations, cudaError_t* cuda_err);
 
+// Force-driven flow with every face periodic (periodic.cu): one pull step,
+// observing when obs; gforce = body acceleration per domain (device).
+cudaError_t launch_periodic_step(int q, int eq, bool obs, HotArgs A, const float* gforce, const float* src,
+                                 float* dst, float* uprev, double* partials, cudaStream_t st);
+
 // Local pore size (pore.cu): exact squared distance to the nearest solid node of
 // a dense mask (d2, tmp: nx*ny*nz uint32 each), then h = 2 D - 1 and the local Kn.
 cudaError_t launch_pore_d2(const uint8_t* mask, int nx, int ny, int nz, uint32_t* d2, uint32_t* tmp,

@@ -101,6 +101,7 @@ def load(path: Optional[str] = None):
         "lbm_qsgs": (i32, [u64, i32, i32, i32, d, d, d, P, P, P]),
         "lbm_qsgs_noalloc": (i32, [u64, i32, i32, i32, d, d, d, P, P, P]),
         "lbm_batch_create": (i32, [i32, P, P, P]),
+        "lbm_batch_create_forced": (i32, [i32, P, P, P, P]),
         "lbm_create_domain": (i32, [P, i32, i32, d, d, P, P]),
         "lbm_create_domain_3d": (i32, [P, i32, i32, i32, d, d, P, P]),
         "lbm_destroy": (None, [P]),
@@ -280,6 +281,23 @@ def lbm_batch_create(masks: Sequence[np.ndarray], taus: Sequence[float], drhos: 
     h = C.c_void_p()
     _check(load().lbm_batch_create(n, descs, C.byref(o), C.byref(h)))
     return Solver(h, masks, taus, drhos, o)
+
+
+def lbm_batch_create_forced(masks: Sequence[np.ndarray], taus: Sequence[float], g: Sequence[float],
+                            options: Optional[lbm_options] = None) -> Solver:
+    """Force-driven domains with every face periodic (body acceleration g[d]
+    along +x); lbm_permeability gives Eq. 2's k = nu <u>/g."""
+    masks = [_mask(m) for m in masks]
+    n = len(masks)
+    descs = (lbm_domain_desc * n)()
+    for d, m in enumerate(masks):
+        nz, ny, nx = (1,) + m.shape if m.ndim == 2 else m.shape
+        descs[d] = lbm_domain_desc(m.ctypes.data, nx, ny, nz, float(taus[d]), 0.0)
+    gg = np.ascontiguousarray(g, np.float64)
+    o = options if options is not None else make_options()
+    h = C.c_void_p()
+    _check(load().lbm_batch_create_forced(n, descs, _ptr(gg), C.byref(o), C.byref(h)))
+    return Solver(h, masks, taus, [0.0] * n, o)
 
 
 def lbm_create_domain(mask, tau: float, drho: float, options: Optional[lbm_options] = None) -> Solver:
