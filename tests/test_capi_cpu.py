@@ -111,3 +111,30 @@ def test_load_rejects_missing_and_corrupt_files(lib, tmp_path):
     p = tmp_path / "bad.ckpt"
     p.write_bytes(b"LBMGB300" + b"\x00" * 7)
     assert lib.lbm_load(str(p).encode(), C.byref(o), C.byref(h)) == lbm.LBM_ERR_IO
+
+
+def test_forced_create_rejects_bad_arguments(lib):
+    m = np.zeros((6, 9), np.uint8)
+    desc = (lbm.lbm_domain_desc * 1)()
+    desc[0] = lbm.lbm_domain_desc(m.ctypes.data, 9, 6, 1, 0.8, 0.0)
+    h = C.c_void_p()
+    o = lbm.make_options()
+    assert lib.lbm_batch_create_forced(1, desc, None, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+    g = np.array([np.nan])
+    assert lib.lbm_batch_create_forced(1, desc, g.ctypes.data, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+    g = np.array([1e-5])
+    t = lbm.make_options(collision=lbm.LBM_COLL_TRT)
+    assert lib.lbm_batch_create_forced(1, desc, g.ctypes.data, C.byref(t), C.byref(h)) == lbm.LBM_ERR_ARG
+    assert h.value is None
+
+
+def test_trt_options_are_validated(lib):
+    m = np.zeros((6, 9), np.uint8)
+    h = C.c_void_p()
+    for kw in (dict(collision=2), dict(collision=1, trt_lambda=0.0), dict(collision=1, trt_lambda=float("inf"))):
+        o = lbm.make_options(**kw)
+        assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+
+
+def test_local_knudsen_rejects_null_handle(lib):
+    assert lib.lbm_local_knudsen(None, 0, None, None, None) == lbm.LBM_ERR_ARG
