@@ -172,7 +172,7 @@ def measured_hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "lbm_device.cuh"):
+    for f in ("lbm_kernels.cu", "aa_kernels.cu", "lbm_stencil.cuh", "lbm_device.cuh"):
         with open(os.path.join(ROOT, "paper_1609_09685_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -1,0 +1,235 @@
+// lbm_stencil.cuh -- device helpers shared by the pull kernel (lbm_kernels.cu)
+// and the in-place pair kernels (aa_kernels.cu): neighbour windows, source
+// slots, Zou-He, moments, the collision of an opposite pair, cp.async.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "lbm_device.cuh"
+
+namespace lbmgb {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SegLoc {
+    int s, y, z, x;
+};
+
+__device__ __forceinline__ SegLoc locate(const DomainDev& D, uint32_t gseg, int lane) {
+    const uint32_t local = gseg - D.seg_base;
+    const uint32_t nseg = (uint32_t)D.nseg;
+    SegLoc L;
+    L.s = (int)(local % nseg);
+    const uint32_t row = local / nseg;
+    L.y = (int)(row % (uint32_t)D.ny);
+    L.z = (int)(row / (uint32_t)D.ny);
+    L.x = L.s * kSegW + lane;
+    return L;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Zou-He pressure closure in shifted form for the face whose inward normal is
+// `SIDE` (+1 at x = 0, -1 at x = N_x - 1), u_y = u_z = 0:
+//   rho u_x = side * (drho_b - (S_0 + 2 S_in)),  S_0 = sum over c_x = 0,
+//   S_in = sum over the known directions c_x = -side,
+//   N_a = 1/2 sum_{c_x = 0} c_a g (transverse momentum of the c_x = 0 set),
+//   g_i = g_opp(i) + side 6 w_i rho u_x - c_iy N_y - c_iz N_z  for c_ix = side.
+// Written generically; in 2D it reduces to Zou & He (1997), in 3D to the
+// Hecht & Harting (2010) form.  The shifted weights cancel because the c_x = 0
+// weights plus twice the c_x = -side weights sum to one.
+template <class L, int SIDE>
+__device__ __forceinline__ void zou_he(float (&f)[L::Q], float drho_b) {
+    float s0 = 0.f, sin = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        if (L::c(i, 0) == 0) {
+            s0 += f[i];
+            ny += (float)L::c(i, 1) * f[i];
+            nz += (float)L::c(i, 2) * f[i];
+        } else if (L::c(i, 0) == -SIDE) {
+            sin += f[i];
+        }
+    }
+    const float rux = (float)SIDE * (drho_b - (s0 + 2.f * sin));
+    ny *= 0.5f;
+    nz *= 0.5f;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        if (L::c(i, 0) == SIDE) {
+            const float w6 = (float)(6.0 * L::wd(i));
+            f[i] = f[opp<L>(i)] + (float)SIDE * w6 * rux - (float)L::c(i, 1) * ny -
+                   (float)L::c(i, 2) * nz;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Fused stream + boundaries + BGK collide; OBS adds the per-interval FP64
+// reductions (flux, residual terms, max |u|, non-finite count, mass).
+//
+// A warp walks one strip (consecutive rows of one segment column).  For each
+// row it reads the neighbour window of every row it pulls from (the row above,
+// its own, the row below; in 3D also the planes in front and behind).  Lane l
+// shifts the 34-bit window by l: bits 0, 1, 2 are the fluid flags of the
+// sources at x - 1, x, x + 1, i.e. for c_x = +1, 0, -1, and the compact index
+// of the c_x = +1 source is the window base plus a popcount below lane l.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Win {
+    uint32_t tri;  // fluid flags of nodes x - 1, x, x + 1 in the window's row
+    uint32_t i0;   // compact index of node x - 1 (valid when that node is fluid)
+};
+
+__device__ __forceinline__ Win make_win(const uint4 r, int lane, uint32_t lmask) {
+    const uint64_t W = ((uint64_t)r.y << 32) | r.x;
+    Win w;
+    w.tri = (uint32_t)(W >> lane) & 7u;
+    w.i0 = r.z + __popc(r.x & lmask);
+    return w;
+}
+template <int CX>
+__device__ __forceinline__ uint32_t win_idx(const Win& w) {
+    return CX == 1 ? w.i0 : (CX == 0 ? w.i0 + (w.tri & 1u) : w.i0 + (w.tri & 1u) + ((w.tri >> 1) & 1u));
+}
+template <int CX>
+__device__ __forceinline__ bool win_fluid(const Win& w) {
+    return (w.tri >> (1 - CX)) & 1u;
+}
+// c_i . v using only the non-zero components of c_i (without fast-math the
+// compiler must keep 0 * v, which is not 0 for a non-finite v).
+template <class L>
+__device__ __forceinline__ float cdot(int i, float vx, float vy, float vz) {
+    float r = 0.f;
+    if (L::c(i, 0) > 0) r += vx;
+    if (L::c(i, 0) < 0) r -= vx;
+    if (L::c(i, 1) > 0) r += vy;
+    if (L::c(i, 1) < 0) r -= vy;
+    if (L::c(i, 2) > 0) r += vz;
+    if (L::c(i, 2) < 0) r -= vz;
+    return r;
+}
+// first moments: density deviation and the momentum components, from the
+// non-zero velocity components only
+template <class L>
+__device__ __forceinline__ void moments(const float (&f)[L::Q], float& dr, float& jx, float& jy, float& jz) {
+    dr = 0.f;
+    jx = 0.f;
+    jy = 0.f;
+    jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        dr += f[i];
+        if (L::c(i, 0) > 0) jx += f[i];
+        if (L::c(i, 0) < 0) jx -= f[i];
+        if (L::c(i, 1) > 0) jy += f[i];
+        if (L::c(i, 1) < 0) jy -= f[i];
+        if (L::c(i, 2) > 0) jz += f[i];
+        if (L::c(i, 2) < 0) jz -= f[i];
+    }
+}
+
+// Post-collision values of the opposite pair (i, opp i) from the pair's even
+// and odd equilibrium terms sym = omega w (even part of f_eq - w rho_0) and
+// anti = omega_m 3 w (c_i . j).  BGK (omega_m == omega, warp-uniform per
+// domain): f* = (1 - omega) f + sym +- anti.  TRT (Ginzburg 2005): the even
+// part (f_i + f_o)/2 relaxes with omega, the odd part (f_i - f_o)/2 with
+// omega_m; hw = omega/2, hwm = omega_m/2.
+__device__ __forceinline__ void pair_relax(float fi, float fo, float sym, float anti, float omc, float hw,
+                                           float hwm, bool trt, float& oi, float& oo) {
+    if (!trt) {
+        oi = fmaf(omc, fi, sym + anti);
+        oo = fmaf(omc, fo, sym - anti);
+    } else {
+        const float hp = hw * (fi + fo), hm = hwm * (fi - fo);
+        oi = (fi - hp - hm) + (sym + anti);
+        oo = (fo - hp + hm) + (sym - anti);
+    }
+}
+
+template <int I, class L>
+struct Dir {
+    static constexpr int cx = L::c(I, 0), cy = L::c(I, 1), cz = L::c(I, 2);
+    static constexpr int o = opp<L>(I);
+    static constexpr int fy = flip<L>(I, true, false), fz = flip<L>(I, false, true),
+                         fyz = flip<L>(I, true, true);
+    static constexpr int row = (1 - cy) + (L::NROW == 9 ? 3 * (1 - cz) : 0);
+};
+
+// Source element of direction I for the node of window set w (pull
+// streaming): the fluid source's compact slot in the (possibly mirrored)
+// direction plane, or the node's own opposite slot when the source is solid
+// (bounce-back).  Plane offsets are compile-time multiples of the uniform
+// plane stride, so they stay in uniform registers.
+template <class L, int I>
+__device__ __forceinline__ uint32_t src_elem(const Win (&w)[L::NROW], uint32_t PS, uint32_t kd, bool my, bool mz) {
+    using d = Dir<I, L>;
+    const Win& wn = w[d::row];
+    const bool sf = win_fluid<d::cx>(wn);
+    uint32_t plane = (uint32_t)I * PS;
+    if (d::cy != 0 && d::cz != 0)
+        plane = my ? (mz ? (uint32_t)d::fyz * PS : (uint32_t)d::fy * PS) : (mz ? (uint32_t)d::fz * PS : plane);
+    else if (d::cy != 0) plane = my ? (uint32_t)d::fy * PS : plane;
+    else if (d::cz != 0) plane = mz ? (uint32_t)d::fz * PS : plane;
+    return sf ? plane + win_idx<d::cx>(wn) : (uint32_t)d::o * PS + kd;
+}
+
+// Bit i set when the pull source of direction i is fluid.  The destination of
+// direction i is the source of opp(i), so bit opp(i) tells whether a
+// post-collision population in direction i reaches a fluid node.
+template <class L, int... Is>
+__device__ __forceinline__ uint32_t src_fluid_mask(const Win (&w)[L::NROW], std::integer_sequence<int, Is...>) {
+    return ((win_fluid<Dir<Is, L>::cx>(w[Dir<Is, L>::row]) ? (1u << Is) : 0u) | ...);
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const float* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue the Q source loads of one row into shared-memory stage `sbase`
+// (slot (i, lane) at sbase + 4 (32 i + lane)).  For a solid lane kd is the
+// slot of the next fluid node (at most the padding slot nfluid < pstride), so
+// every address is in bounds; the value is discarded.
+template <class L, int... Is>
+__device__ __forceinline__ void issue_row(const float* __restrict__ src, uint32_t PS, const Win (&w)[L::NROW],
+                                          uint32_t kd, bool ylo, bool yhi, bool zlo, bool zhi, uint32_t sbase,
+                                          std::integer_sequence<int, Is...>) {
+    // a direction with c_y = +1 pulls from row y - 1, mirrored when y = 0, etc.
+    (cp_async4(sbase + 4u * (32u * Is),
+               src + src_elem<L, Is>(w, PS, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, Dir<Is, L>::cz > 0 ? zlo : zhi)),
+     ...);
+}
+
+}  // namespace
+
+}  // namespace lbmgb
