@@ -262,8 +262,11 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs);
  * of 10 checks, with D1 and D0 the last two changes of k and q = |D1/D0|, the
  * remaining error of a geometric approach is at most |D1| q/(1 - q); the
  * domain stops once that bound is below opt.k_tol |k| at 10 consecutive checks
- * with r < 10 opt.k_tol, or once k has stayed within 0.05 opt.k_tol |k| over 40
- * checks (|k| is taken
+ * with r < 10 opt.k_tol (or with |k| below 1e-3 of its largest value in the
+ * run: a flow that dies out keeps r of order one), once k has stayed within
+ * 0.05 opt.k_tol |k| over 40 checks, or once |k| has stayed below
+ * 0.1 opt.k_tol times its largest value for 10 checks (no connected fluid
+ * path: k -> 0) (|k| is taken
  * as at least 1e-3 of its largest value in the run, so that a domain whose
  * flow dies out, having no through-path, stops too).  This is the
  * stop that matters in FP32: in the Stokes regime the per-node residual

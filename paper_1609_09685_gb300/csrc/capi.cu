@@ -43,6 +43,7 @@ struct DomainHost {
     std::vector<double> rhist;
     std::vector<double> kq;   // recent k values for the k-based stop
     int32_t k_ok = 0;         // consecutive checks meeting the k-based stop
+    int32_t k_dead = 0;       // consecutive checks with |k| below 0.1 k_tol of its peak
     double k_peak = 0.0;      // largest |k| seen in this run
     bool has_obs = false;
     double obs[kNumObs] = {0};
@@ -390,7 +391,10 @@ bool k_converged(DomainHost& D, double k, double r, double k_tol) {
     D.k_peak = std::max(D.k_peak, std::fabs(k));
     const double tolk = k_tol * std::max(std::fabs(k), 1e-3 * D.k_peak);
     bool ok = false;
-    if (n >= 2 * W + 1 && r < 10.0 * k_tol) {
+    // a flow that dies out (no connected fluid path) keeps a relative residual
+    // of order one while it decays, so the residual gate does not apply there
+    const bool vanishing = std::fabs(k) < 1e-3 * D.k_peak;
+    if (n >= 2 * W + 1 && (r < 10.0 * k_tol || vanishing)) {
         const double d1 = D.kq[n - 1] - D.kq[n - 1 - W], d0 = D.kq[n - 1 - W] - D.kq[n - 1 - 2 * W];
         if (d0 != 0.0) {
             const double q = std::fabs(d1 / d0);
@@ -401,6 +405,9 @@ bool k_converged(DomainHost& D, double k, double r, double k_tol) {
     }
     D.k_ok = ok ? D.k_ok + 1 : 0;
     if (D.k_ok >= 10) return true;
+    // vanishing flow: |k| below 0.1 k_tol of its peak for 10 checks in a row
+    D.k_dead = (std::fabs(k) < 0.1 * k_tol * D.k_peak) ? D.k_dead + 1 : 0;
+    if (D.k_dead >= 10) return true;
     if (n == KEEP) {
         double lo = D.kq[0], hi = D.kq[0];
         for (double v : D.kq) {
@@ -886,6 +893,7 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
         D.rhist.clear();
         D.kq.clear();
         D.k_ok = 0;
+        D.k_dead = 0;
         D.k_peak = 0.0;
         D.h_step.clear();
         D.h_k.clear();

@@ -492,3 +492,27 @@ def test_forced_solver_rejects_pressure_only_calls(tmp_path):
     with lbm.lbm_batch_create_forced([mask], [0.8], [1e-5]) as s:
         with pytest.raises(lbm.LBMError):
             lbm.lbm_save(s, str(tmp_path / "x.ckpt"))
+
+
+def test_degenerate_domains_in_a_batch():
+    """An all-solid domain (no fluid node at all) and a domain whose fluid
+    does not connect inlet to outlet, batched with a normal one: the normal
+    domain matches its separate oracle run, the all-solid one holds nothing,
+    and the blocked one converges to zero flux (k = 0)."""
+    normal, _ = O.qsgs((20, 48), 2, 0.02, 0.7)
+    solid = np.ones((8, 40), np.uint8)
+    blocked = np.zeros((10, 40), np.uint8)
+    blocked[:, 20] = 1  # a solid wall across the channel
+    masks = [normal, solid, blocked]
+    taus, drhos = [0.8, 0.9, 0.7], [1e-3, 1e-3, 1e-3]
+    with lbm.lbm_batch_create(masks, taus, drhos) as s:
+        assert lbm.lbm_domain_fluid_nodes(s, 1) == 0
+        lbm.lbm_step(s, 9)
+        ref = O.run(normal, O.init(normal, 1 + drhos[0], 1.0), taus[0], 1 + drhos[0], 1.0, 9)
+        _assert_close(lbm.lbm_get_populations(s, 0), ref, 9, normal)
+        assert np.all(lbm.lbm_get_populations(s, 1) == 0.0)
+        rc, st, steps, res = lbm.lbm_run_to_steady(s, 1e-7, 400000)
+        k, _ = lbm.lbm_permeability(s)
+    assert st[1] == lbm.LBM_OK and st[2] in (lbm.LBM_OK, lbm.LBM_STALLED)
+    assert k[1] == 0.0
+    assert abs(k[2]) < 1e-6 * abs(k[0])
