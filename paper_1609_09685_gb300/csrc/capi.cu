@@ -89,6 +89,7 @@ struct lbm_solver {
     uint32_t nvitems = 0;
     uint32_t* d_face = nullptr;  // inlet/outlet bits per compact slot
     bool forced = false;         // force-driven, every face periodic (lbm_batch_create_forced)
+    bool obs_only = false;       // the last observation was taken without stepping
     float* d_gforce = nullptr;   // body acceleration per domain (force-driven solvers)
     uint32_t nitems = 0;
     uint8_t* d_mask = nullptr;
@@ -324,6 +325,7 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
         h->cur ^= 1;
     }
     if (obs) {
+        h->obs_only = (n == 0);
         if (n == 0) CK(h, launch_observe(h->q, G, h->d_g[h->cur], h->d_uprev, h->d_partials, h->st));
         CK(h, launch_reduce_obs(h->d_dom, (int)h->dom.size(), h->d_partials, h->d_obs, n > 0, h->st));
         CK(h, cudaMemcpyAsync(h->h_obs, h->d_obs, sizeof(double) * kNumObs * h->dom.size(),
@@ -365,6 +367,11 @@ void store_obs(lbm_handle h) {
     for (size_t d = 0; d < h->dom.size(); ++d) {
         if (!h->dom[d].active) continue;
         std::memcpy(h->dom[d].obs, h->h_obs + d * kNumObs, sizeof(double) * kNumObs);
+        // An observation without a step comes from the pressure-driven observe
+        // kernel (slot 0 = link flux).  For force-driven solvers slot 0 must be
+        // the Eq. 2 flux: the stored momentum (slot 6) plus F/2 per fluid node.
+        if (h->forced && h->obs_only)
+            h->dom[d].obs[0] = h->dom[d].obs[6] + 0.5 * h->dom[d].g * h->opt.rho_out * h->dom[d].fluid_count;
         h->dom[d].has_obs = true;
     }
 }

@@ -516,3 +516,21 @@ def test_degenerate_domains_in_a_batch():
     assert st[1] == lbm.LBM_OK and st[2] in (lbm.LBM_OK, lbm.LBM_STALLED)
     assert k[1] == 0.0
     assert abs(k[2]) < 1e-6 * abs(k[0])
+
+
+def test_forced_observation_without_stepping_gives_eq2_flux():
+    """An observation taken without a step on a force-driven solver reports
+    Eq. 2's flux, so lbm_permeability agrees with the oracle's Eq. 2 on the
+    same (GPU) populations, before and after stepping."""
+    mask, _ = O.qsgs((6, 8, 20), 3, 0.05, 0.75)
+    tau, g = 0.9, 1e-4
+    with lbm.lbm_batch_create_forced([mask], [tau], [g]) as s:
+        lbm.lbm_step(s, 40)
+        lbm.lbm_step_observe(s, 0)
+        k, _ = lbm.lbm_permeability(s)
+        f = lbm.lbm_get_populations(s, 0)
+        assert k[0] == pytest.approx(O.permeability_forced(mask, f, tau, g), rel=1e-5)
+        lbm.lbm_step_observe(s, 1)
+        k, _ = lbm.lbm_permeability(s)
+        f = lbm.lbm_get_populations(s, 0)
+        assert k[0] == pytest.approx(O.permeability_forced(mask, f, tau, g), rel=1e-5)
