@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="sweep")
     p.add_argument("--interval", type=int, default=100)
+    p.add_argument("--kn-sweep", action="store_true",
+                   help="also solve the 24 tau-sweep domains to steady state (BGK and TRT) and report k/k_int vs Kn")
     p.add_argument("--forced3d", action="store_true",
                    help="also run the paper's force-driven periodic 3D experiment (100^3, phi 0.748587)")
     p.add_argument("--local-kn", action="store_true",
@@ -325,6 +327,55 @@ def measure_warmstart(args, lbm, sp):
     }
 
 
+def measure_kn_sweep(lbm, sp):
+    """Sec. 2's Figs. 2-3: k / k_int against Kn on the tau sweep at the three
+    resolutions.  Two normalisers are reported: TRT's permeability with
+    Lambda = 3/16, which does not depend on tau, and BGK's k extrapolated to
+    tau -> 1/2 by a least-squares line in (tau - 1/2)^2 (the form of the exact
+    channel solution)."""
+    import torch
+    wl = get_workload("sweep", 0)
+    cache, masks = {}, []
+    for d in wl.domains:
+        key = (d.shape, d.seed, d.porosity)
+        if key not in cache:
+            cache[key], _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity, d.d_face, stream=sp)
+        masks.append(cache[key])
+    taus = [d.tau for d in wl.domains]
+    drhos = [d.drho for d in wl.domains]
+    out = {"workload": wl.name, "tol": 1e-9}
+    for name, coll in (("bgk", lbm.LBM_COLL_BGK), ("trt", lbm.LBM_COLL_TRT)):
+        s = lbm.lbm_batch_create(masks, taus, drhos, lbm.make_options(stream=sp, collision=coll))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st, steps, _ = lbm.lbm_run_to_steady(s, 1e-9, 3_000_000)
+        torch.cuda.synchronize()
+        k, kn = lbm.lbm_permeability(s)
+        out[name] = {"seconds": time.perf_counter() - t0, "k": [float(v) for v in k], "kn": [float(v) for v in kn],
+                     "status": [int(v) for v in st], "steps": [int(v) for v in steps]}
+        s.close()
+    res = {}
+    for nx in sorted({d.nx for d in wl.domains}):
+        idx = [i for i, d in enumerate(wl.domains) if d.nx == nx]
+        t2 = np.array([(taus[i] - 0.5) ** 2 for i in idx])
+        kb = np.array([out["bgk"]["k"][i] for i in idx])
+        A = np.vstack([np.ones_like(t2), t2]).T
+        use = t2 <= 0.25  # the small-Kn end, where the (tau - 1/2)^2 form holds best
+        coef, *_ = np.linalg.lstsq(A[use], kb[use], rcond=None)
+        k_int = float(coef[0])
+        k_trt = float(np.mean([out["trt"]["k"][i] for i in idx]))
+        res[f"{nx}x{nx // 2}"] = {
+            "k_int_bgk_extrapolated": k_int,
+            "k_trt_mean": k_trt,
+            "k_over_k_trt_bgk": [float(v / k_trt) for v in kb],
+            "k_trt_spread": float(np.ptp([out["trt"]["k"][i] for i in idx]) / np.mean([out["trt"]["k"][i] for i in idx])),
+            "kn": [out["bgk"]["kn"][i] for i in idx],
+            "k_over_k_int_bgk": [float(v / k_int) for v in kb],
+        }
+    out["per_resolution"] = res
+    return out
+
+
 def measure_forced3d(lbm, sp):
     """Sec. 2's 3D experiment: a 100^3 QSGS medium at porosity 0.748587, driven
     by three body accelerations with every face periodic; k = nu <u>/g (Eq. 2)
@@ -509,6 +560,7 @@ def run_native(args):
     s.close()
     ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
     f3d = measure_forced3d(lbm, sp) if (args.forced3d and rank == 0) else None
+    kns = measure_kn_sweep(lbm, sp) if (args.kn_sweep and rank == 0) else None
     ws = measure_warmstart(args, lbm, sp) if (args.warmstart and rank == 0) else None
 
     if rank == 0:
@@ -574,6 +626,8 @@ def run_native(args):
             line["local_knudsen"] = lkn
         if f3d is not None:
             line["forced_3d"] = f3d
+        if kns is not None:
+            line["kn_sweep"] = kns
         if ws is not None:
             line["warm_start"] = ws
         print(json.dumps(line), flush=True)
