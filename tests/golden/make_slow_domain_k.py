@@ -1,7 +1,7 @@
 """Writes slow_domain_k.txt: the FP64 oracle's permeability of one 512x256
 QSGS domain whose slowest pressure mode relaxes over ~5e4 steps, after exactly
 250000 steps from the equilibrium start (the oracle's own k changes by < 1e-6
-relative after that).  Calls only oracle/.  Takes about 45 minutes on one core:
+relative after that).  Calls only oracle/.  Takes about an hour on one core:
 
     python tests/golden/make_slow_domain_k.py
 """
