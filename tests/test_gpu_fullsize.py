@@ -150,3 +150,42 @@ def test_slow_512x256_domain_keeps_k_within_1e4_of_fp64():
         assert lbm.lbm_get_step(s) == steps
         k, _ = lbm.lbm_permeability(s)
     assert k[0] == pytest.approx(k_ref, rel=1e-4)
+
+
+def test_trt_tau_sweep_pair_parity_full_size():
+    """TRT (Lambda = 3/16) on the full tau-sweep batch: one in-place pair on
+    sampled domains against two FP64 oracle TRT steps from the GPU's state."""
+    wl = workloads.tau_sweep()
+    masks = _masks(wl)
+    lam = 3.0 / 16.0
+    opts = lbm.make_options(collision=lbm.LBM_COLL_TRT, trt_lambda=lam)
+    with lbm.lbm_batch_create(masks, [d.tau for d in wl.domains], [d.drho for d in wl.domains], opts) as s:
+        lbm.lbm_step(s, 60)
+        w = O.lattice(9)[1]
+        for d in (0, 15, 23):
+            dom = wl.domains[d]
+            f = lbm.lbm_get_populations(s, d)
+            ref = O.run(masks[d], f, dom.tau, 1.0 + dom.drho, 1.0, 2, tau_m=O.tau_minus(dom.tau, lam))
+            lbm.lbm_step(s, 2)
+            g = lbm.lbm_get_populations(s, d)
+            fluid = ~masks[d].astype(bool)
+            a, b = (g - w)[fluid], (ref - w)[fluid]
+            assert np.abs(a - b).max() <= 2 * REL * np.abs(b).max(), d
+
+
+def test_forced_3d_experiment_domain_one_step_parity():
+    """The force-driven 100^3 domain of the 3D experiment: one step of the
+    periodic kernel against the oracle from the GPU's state, for both
+    equilibria."""
+    mask, _ = lbm.lbm_qsgs(1, (100, 100, 100), 0.02, 0.748587)
+    w = O.lattice(19)[1]
+    fluid = ~mask.astype(bool)
+    for eq in (0, 1):
+        with lbm.lbm_batch_create_forced([mask], [1.0], [1e-3], lbm.make_options(equilibrium=eq)) as s:
+            lbm.lbm_step(s, 20)
+            f = lbm.lbm_get_populations(s, 0)
+            ref = O.step_forced(mask, f, 1.0, 1e-3, eq)
+            lbm.lbm_step(s, 1)
+            g = lbm.lbm_get_populations(s, 0)
+        a, b = (g - w)[fluid], (ref - w)[fluid]
+        assert np.abs(a - b).max() <= REL * np.abs(b).max(), eq
