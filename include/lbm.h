@@ -6,7 +6,9 @@
  * permeability", arXiv:1609.09685) do in Sec. 2: a BGK lattice Boltzmann run of
  * pressure-driven flow along x (D2Q9 in 2D, D3Q19 in 3D), iterated to steady
  * state, with the permeability taken from the simulated mass flow rate by
- * Darcy's law and reported against Kn = sqrt(pi/6) (tau - 1/2) / N_x.
+ * Darcy's law and reported against Kn = sqrt(pi/6) (tau - 1/2) / N_x.  It also
+ * runs the paper's force-driven periodic 3D setup (Eq. 2), a TRT collision and
+ * local pore-size / local-Kn diagnostics.
  *
  * Every lattice update, reduction, mask-generation and field conversion step
  * runs in the library's own CUDA kernels (sm_103a).  Host code only validates
@@ -78,10 +80,10 @@ typedef struct lbm_options {
     double stall_floor;      /* stall rule applies only while r < stall_floor (default 1e-5) */
     double rho_out;          /* outlet density rho_0 (default 1.0) */
     void* stream;            /* cudaStream_t; NULL = legacy default stream */
-    int32_t block_threads;   /* stream-collide block size, a multiple of 32 up to 256; 0 = 128 */
+    int32_t block_threads;   /* block size of the step kernels, a multiple of 32 up to 256; 0 = 128 */
     int32_t use_graphs;      /* capture each check interval as a CUDA graph (default 1) */
     volatile const int32_t* cancel_flag; /* host flag polled between intervals; nonzero cancels */
-    int32_t strip_rows;      /* rows per stream-collide work item (0 = default 8, max 255) */
+    int32_t strip_rows;      /* rows per work item of the pull and gather steps (0 = default 8, max 255) */
     double k_tol;            /* permeability-based stop (see lbm_run_to_steady); 0 disables (default 1e-5) */
     int32_t in_place_pairs;  /* 1 (default): advance plain steps two at a time in place (a gather step that
                                 writes each result back to the slot it read, then a step on each node's own
