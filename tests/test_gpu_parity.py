@@ -534,3 +534,13 @@ def test_forced_observation_without_stepping_gives_eq2_flux():
         k, _ = lbm.lbm_permeability(s)
         f = lbm.lbm_get_populations(s, 0)
         assert k[0] == pytest.approx(O.permeability_forced(mask, f, tau, g), rel=1e-5)
+
+
+def test_solve_sharded_without_a_process_group_runs_the_whole_list():
+    from paper_1609_09685_gb300 import sharding
+    masks = [O.qsgs((20, 40), 1, 0.02, 0.7)[0], O.qsgs((16, 48), 2, 0.02, 0.72)[0]]
+    k, st = sharding.solve_sharded(masks, [0.8, 1.0], [1e-3, 1e-3], tol=1e-8, max_steps=200000)
+    with lbm.lbm_batch_create(masks, [0.8, 1.0], [1e-3, 1e-3]) as s:
+        lbm.lbm_run_to_steady(s, 1e-8, 200000)
+        k2, _ = lbm.lbm_permeability(s)
+    assert np.array_equal(k, k2) and np.all(st == 0)
