@@ -319,7 +319,7 @@ lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const floa
  * global step counter, permeability k(t) from that interval's flux (as
  * lbm_permeability), residual r, and host seconds since the call began.  Up to
  * `capacity` entries are written to each non-null array; *count receives the
- * number recorded.  Used to judge time-to-permeability a posteriori. */
+ * number recorded.  Used to measure time-to-permeability a posteriori. */
 lbm_status lbm_get_history(lbm_handle h, int32_t d, int64_t* steps, double* k, double* residual,
                            double* seconds, int32_t capacity, int32_t* count);
 

@@ -2,7 +2,7 @@
 // porous mask (plus tau and an x ramp) to the normalised steady fields
 // (rho - rho_out)/drho and u nu (N_x - 1)/(c_s^2 drho), trained and run on the
 // GPU.  Its prediction only initialises the populations; the lattice Boltzmann
-// iteration then converges from there and judges the error (the paper's
+// iteration then converges from there and removes its error (the paper's
 // method is unchanged; the network is an accelerator of its steady state).
 //
 // Tensors are NHWC: activations bf16 with channel counts that are multiples
