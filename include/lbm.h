@@ -193,7 +193,7 @@ lbm_status lbm_create_domain_3d(const uint8_t* mask, int32_t nx, int32_t ny, int
 /* Synchronises the solver's stream and frees its resources.  Device memory of
  * solvers comes from one stream-ordered pool per device; up to 8 GB of freed
  * blocks stay cached there for the next solver, the rest returns to the
- * driver at the next synchronisation. */
+ * CUDA driver at the next synchronisation. */
 void lbm_destroy(lbm_handle h);
 
 /* Number of domains, lattice size Q, and fluid node count of domain d. */

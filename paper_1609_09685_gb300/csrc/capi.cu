@@ -152,8 +152,8 @@ lbm_status cuda_fail(lbm_handle h, cudaError_t e, const char* what) {
 
 // Device memory of solvers comes from one stream-ordered pool per device.  The
 // pool keeps up to kPoolKeep bytes of freed blocks, so creating and destroying
-// solvers in a loop reuses memory instead of returning it to the driver each
-// time; larger frees go back to the driver at the next synchronisation.
+// solvers in a loop reuses memory instead of returning it to the CUDA driver each
+// time; larger frees go back to the CUDA driver at the next synchronisation.
 constexpr uint64_t kPoolKeep = 8ull << 30;
 
 cudaError_t solver_pool(cudaMemPool_t* pool) {
