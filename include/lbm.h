@@ -175,9 +175,10 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_o
  * doubles) instead of the pressure boundaries.  Solids bounce back half way;
  * the forcing is Guo, Zheng & Shi (2002) with force density F = rho_out g;
  * lbm_permeability then returns Eq. 2's k = nu <u>/g, <u> the sum over fluid
- * nodes of rho u_x over rho_out N_grid (rho u_x of the stored post-collision
- * state plus F/2).  BGK only (opt->collision must be LBM_COLL_BGK); steps are
- * pull steps of a kernel of their own (opt->in_place_pairs is ignored).
+ * nodes of rho u_x over rho_out N_grid, with rho u the fluid momentum of Guo's
+ * scheme (the pre-collision momentum plus F/2, i.e. the stored post-collision
+ * momentum minus F/2).  BGK or TRT (opt->collision); steps are pull steps of a
+ * kernel of their own (opt->in_place_pairs is ignored).
  * lbm_save, lbm_nn_targets and lbm_warm_start return LBM_ERR_ARG on such a
  * solver.
  */

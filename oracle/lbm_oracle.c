@@ -313,10 +313,12 @@ int oc_step_trt(int q, int nx, int ny, int nz, const uint8_t* solid, double tau,
  *   S_i = 3 w_i c_i . F                                                (linear).
  * With the linear (Stokes) equilibrium every term is linear in (f, g).
  */
-int oc_step_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double g, int eq,
-                   const double* fin, double* fout) {
+static int step_forced_impl(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+                            int trt, double g, int eq, const double* fin, double* fout) {
     lattice L;
-    if (get_lattice(q, &L) || nx < 1 || ny < 1 || nz < 1 || (q == 9 && nz != 1) || !(tau > 0.5)) return -1;
+    if (get_lattice(q, &L) || nx < 1 || ny < 1 || nz < 1 || (q == 9 && nz != 1) || !(tau > 0.5) ||
+        !(tau_minus > 0.5))
+        return -1;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -339,29 +341,58 @@ int oc_step_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double t
                 const double F[3] = {g, 0.0, 0.0}; /* rho_0 g, rho_0 = 1 */
                 const double js[3] = {j[0] + 0.5 * F[0], j[1], j[2]};
                 const double us[3] = {js[0] / rho, js[1] / rho, js[2] / rho};
+                double S[19], E[19];
                 for (int i = 0; i < q; ++i) {
                     const double cF = L.c[i][0] * F[0] + L.c[i][1] * F[1] + L.c[i][2] * F[2];
-                    double S;
                     if (eq == EQ_LINEAR) {
-                        S = 3.0 * L.w[i] * cF;
+                        S[i] = 3.0 * L.w[i] * cF;
                     } else {
                         const double cu = L.c[i][0] * us[0] + L.c[i][1] * us[1] + L.c[i][2] * us[2];
                         const double uF = us[0] * F[0] + us[1] * F[1] + us[2] * F[2];
-                        S = L.w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+                        S[i] = L.w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
                     }
-                    out[i] = f[i] - (f[i] - feq(&L, i, rho, js, eq)) / tau + (1.0 - 0.5 / tau) * S;
+                    E[i] = feq(&L, i, rho, js, eq);
+                }
+                for (int i = 0; i < q; ++i) {
+                    if (!trt) {
+                        out[i] = f[i] - (f[i] - E[i]) / tau + (1.0 - 0.5 / tau) * S[i];
+                    } else {
+                        /* TRT: even and odd parts of f - f_eq and of the source
+                         * relax with 1/tau and 1/tau_minus */
+                        const int o = L.opp[i];
+                        const double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+                        const double ep = 0.5 * (E[i] + E[o]), em = 0.5 * (E[i] - E[o]);
+                        const double sp = 0.5 * (S[i] + S[o]), sm = 0.5 * (S[i] - S[o]);
+                        out[i] = f[i] - (fp - ep) / tau - (fm - em) / tau_minus + (1.0 - 0.5 / tau) * sp +
+                                 (1.0 - 0.5 / tau_minus) * sm;
+                    }
                 }
             }
     return 0;
 }
 
-int oc_run_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double g, int eq, double* f,
-                  long nsteps) {
+int oc_step_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double g, int eq,
+                   const double* fin, double* fout) {
+    return step_forced_impl(q, nx, ny, nz, solid, tau, tau, 0, g, eq, fin, fout);
+}
+
+/* The same step with the TRT collision (see oc_step_trt); the even and odd
+ * parts of the forcing source take the factors (1 - 1/(2 tau)) and
+ * (1 - 1/(2 tau_minus)). */
+int oc_step_forced_trt(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus,
+                       double g, int eq, const double* fin, double* fout) {
+    return step_forced_impl(q, nx, ny, nz, solid, tau, tau_minus, 1, g, eq, fin, fout);
+}
+
+/* nsteps steps in place on f; tau_minus <= 0 means BGK. */
+int oc_run_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double tau, double tau_minus, double g,
+                  int eq, double* f, long nsteps) {
     long nn = (long)nx * ny * nz * q;
     double* tmp = (double*)malloc(sizeof(double) * nn);
     if (!tmp) return -2;
+    const int trt = tau_minus > 0.0;
     for (long t = 0; t < nsteps; ++t) {
-        int rc = oc_step_forced(q, nx, ny, nz, solid, tau, g, eq, f, tmp);
+        int rc = step_forced_impl(q, nx, ny, nz, solid, tau, trt ? tau_minus : tau, trt, g, eq, f, tmp);
         if (rc) {
             free(tmp);
             return rc;
@@ -373,7 +404,9 @@ int oc_run_forced(int q, int nx, int ny, int nz, const uint8_t* solid, double ta
 }
 
 /* Eq. (2): k = nu <u> / g, <u> the superficial mean of the fluid velocity
- * (rho u_x = j_x + F_x/2, over rho_0) over all N_grid nodes. */
+ * over all N_grid nodes.  With Guo forcing the fluid momentum is the
+ * pre-collision j plus F/2; the stored post-collision state carries j + F,
+ * so rho u_x = j*_x - F_x/2 of the stored populations (over rho_0). */
 double oc_permeability_forced(int q, int nx, int ny, int nz, const uint8_t* solid, const double* f, double tau,
                               double g, double rho0) {
     lattice L;
@@ -384,7 +417,7 @@ double oc_permeability_forced(int q, int nx, int ny, int nz, const uint8_t* soli
         if (solid[n]) continue;
         double rho, j[3];
         moments(&L, f + n * q, &rho, j);
-        sum += j[0] + 0.5 * g * rho0;
+        sum += j[0] - 0.5 * g * rho0;
     }
     const double nu = (tau - 0.5) / 3.0;
     return nu * (sum / (rho0 * (double)nn)) / g;

@@ -79,7 +79,8 @@ def _get():
                 "oc_percolates": (i, [i, i, i, P]),
                 "oc_pore_d2": (i, [i, i, i, P, P]),
                 "oc_step_forced": (i, [i, i, i, i, P, d, d, i, P, P]),
-                "oc_run_forced": (i, [i, i, i, i, P, d, d, i, P, l]),
+                "oc_run_forced": (i, [i, i, i, i, P, d, d, d, i, P, l]),
+                "oc_step_forced_trt": (i, [i, i, i, i, P, d, d, d, i, P, P]),
                 "oc_permeability_forced": (d, [i, i, i, i, P, P, d, d, d]),
                 "oc_local_knudsen": (i, [i, i, i, P, d, P, P]),
             }
@@ -295,23 +296,28 @@ def local_knudsen(mask, tau):
     return h, kn
 
 
-def step_forced(mask, f, tau, g, eq=EQ_QUADRATIC) -> np.ndarray:
+def step_forced(mask, f, tau, g, eq=EQ_QUADRATIC, tau_m=None) -> np.ndarray:
     """One step of force-driven flow with every face periodic (body
-    acceleration g along +x, Guo forcing)."""
+    acceleration g along +x, Guo forcing); tau_m: TRT (None = BGK)."""
     mask = _mask(mask)
     q, nx, ny, nz = _dims(mask)
     fin = np.ascontiguousarray(f, np.float64)
     out = np.zeros_like(fin)
-    if _get().oc_step_forced(q, nx, ny, nz, _p(mask), tau, g, eq, _p(fin), _p(out)):
+    if tau_m is None:
+        rc = _get().oc_step_forced(q, nx, ny, nz, _p(mask), tau, g, eq, _p(fin), _p(out))
+    else:
+        rc = _get().oc_step_forced_trt(q, nx, ny, nz, _p(mask), tau, tau_m, g, eq, _p(fin), _p(out))
+    if rc:
         raise ValueError("bad arguments")
     return out
 
 
-def run_forced(mask, f, tau, g, nsteps, eq=EQ_QUADRATIC) -> np.ndarray:
+def run_forced(mask, f, tau, g, nsteps, eq=EQ_QUADRATIC, tau_m=None) -> np.ndarray:
     mask = _mask(mask)
     q, nx, ny, nz = _dims(mask)
     h = np.array(f, np.float64, copy=True, order="C")
-    if _get().oc_run_forced(q, nx, ny, nz, _p(mask), tau, g, eq, _p(h), int(nsteps)):
+    if _get().oc_run_forced(q, nx, ny, nz, _p(mask), tau, 0.0 if tau_m is None else tau_m, g, eq, _p(h),
+                            int(nsteps)):
         raise ValueError("bad arguments")
     return h
 
@@ -324,7 +330,7 @@ def permeability_forced(mask, f, tau, g, rho0=1.0) -> float:
                                          tau, g, rho0)
 
 
-def run_forced_to_steady(mask, f, tau, g, tol, max_steps, interval=100, eq=EQ_QUADRATIC):
+def run_forced_to_steady(mask, f, tau, g, tol, max_steps, interval=100, eq=EQ_QUADRATIC, tau_m=None):
     """Steps in intervals until the relative velocity change over an interval
     is below tol; returns (f, status, steps, residual), status 0 = converged."""
     mask = _mask(mask)
@@ -333,7 +339,7 @@ def run_forced_to_steady(mask, f, tau, g, tol, max_steps, interval=100, eq=EQ_QU
     prev = np.stack(fields(mask, h)[1:], axis=-1)[fl]
     steps, r = 0, np.inf
     while steps < max_steps:
-        h = run_forced(mask, h, tau, g, interval, eq)
+        h = run_forced(mask, h, tau, g, interval, eq, tau_m)
         steps += interval
         cur = np.stack(fields(mask, h)[1:], axis=-1)[fl]
         den = np.sqrt((cur ** 2).sum())

@@ -369,9 +369,10 @@ void store_obs(lbm_handle h) {
         std::memcpy(h->dom[d].obs, h->h_obs + d * kNumObs, sizeof(double) * kNumObs);
         // An observation without a step comes from the pressure-driven observe
         // kernel (slot 0 = link flux).  For force-driven solvers slot 0 must be
-        // the Eq. 2 flux: the stored momentum (slot 6) plus F/2 per fluid node.
+        // the Eq. 2 flux: the fluid momentum of Guo's scheme is the stored
+        // post-collision momentum (slot 6) minus F/2 per fluid node.
         if (h->forced && h->obs_only)
-            h->dom[d].obs[0] = h->dom[d].obs[6] + 0.5 * h->dom[d].g * h->opt.rho_out * h->dom[d].fluid_count;
+            h->dom[d].obs[0] = h->dom[d].obs[6] - 0.5 * h->dom[d].g * h->opt.rho_out * h->dom[d].fluid_count;
         h->dom[d].has_obs = true;
     }
 }
@@ -553,7 +554,6 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (gforce) {
-        if (o.collision != LBM_COLL_BGK) return fail(nullptr, LBM_ERR_ARG, "force-driven solvers use BGK");
         o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
         for (int d = 0; d < n; ++d)
             if (!std::isfinite(gforce[d])) return fail(nullptr, LBM_ERR_ARG, "g must be finite");

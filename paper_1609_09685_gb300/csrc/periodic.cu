@@ -13,9 +13,10 @@
 //     3 w_i c_i . F (linear), f* = f - omega (f - f_eq(j')) + (1 - omega/2) S_i;
 //     the rest population from the mass balance, as in the pressure-driven
 //     kernels (the forcing adds no mass);
-//   - the observing variant sums rho u_x of the stored post-collision state
-//     plus F/2 (j_x + 3F/2 of the pre-collision momentum) into slot 0, the
-//     Eq. 2 flux.
+//   - TRT (omega_m != omega): the even and odd parts of f - f_eq and of the
+//     source relax with omega and omega_m (factors 1 - omega/2, 1 - omega_m/2);
+//   - the observing variant sums the fluid momentum of Guo's scheme, the
+//     pre-collision j_x plus F/2, into slot 0: the Eq. 2 flux.
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
     const bool wrapl = (s == 0 && lane == 0);                     // x = 0: its x - 1 is N_x - 1
     const bool wrapr = (s == nseg - 1 && lane == lastl);          // x = N_x - 1: its x + 1 is 0
     const float om = D.omega, omc = 1.0f - om, hf = 1.0f - 0.5f * om;
+    const float omm = D.omega_m, hfm = 1.0f - 0.5f * omm;
+    const bool trt = (omm != om);
     const float F = gforce[dom] * D.rho0;
     const float* src = A.src[0];
     float* const dst0 = A.dst[0];
@@ -171,12 +174,10 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
         const float jj = jsx * jsx + jy * jy + jz * jz;
         float dsum = 0.f;
         float* const dk = dst0 + kd;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
+        auto eqs = [&](int i, float& eqi, float& Si) {
             const float wi = (float)L::wd(i);
             const float cj = pdot<L>(i, jsx, jy, jz);
             const float cF = (float)L::c(i, 0) * F;
-            float eqi, Si;
             if (EQ == 0) {
                 eqi = wi * (dr + 3.0f * cj + irho * (4.5f * cj * cj - 1.5f * jj));
                 const float cu = pdot<L>(i, ux, uy, uz);
@@ -185,9 +186,29 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
                 eqi = wi * (dr + 3.0f * cj);
                 Si = 3.0f * wi * cF;
             }
-            const float out = fmaf(omc, f[i], fmaf(om, eqi, hf * Si));
-            dsum += f[i] - out;
-            dk[(uint32_t)i * PS] = out;
+        };
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (opp<L>(i) < i) continue;
+            const int o = opp<L>(i);
+            float ei, si, eo, so;
+            eqs(i, ei, si);
+            eqs(o, eo, so);
+            float oi, oo;
+            if (!trt) {
+                oi = fmaf(omc, f[i], fmaf(om, ei, hf * si));
+                oo = fmaf(omc, f[o], fmaf(om, eo, hf * so));
+            } else {
+                const float fp = 0.5f * (f[i] + f[o]), fm = 0.5f * (f[i] - f[o]);
+                const float ep = 0.5f * (ei + eo), em = 0.5f * (ei - eo);
+                const float sp = 0.5f * (si + so), sm = 0.5f * (si - so);
+                const float even = hf * sp - om * (fp - ep), odd = hfm * sm - omm * (fm - em);
+                oi = f[i] + even + odd;
+                oo = f[o] + even - odd;
+            }
+            dsum += (f[i] - oi) + (f[o] - oo);
+            dk[(uint32_t)i * PS] = oi;
+            dk[(uint32_t)o * PS] = oo;
         }
         dk[0] = f[0] + dsum;  // mass balance
         if (OBS) {
@@ -197,7 +218,7 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
             const float pz = (L::D == 3) ? uprev[2u * PS + kd] : 0.f;
             const float ex = pux - px, ey = puy - py, ez = puz - pz;
             const float uu = pux * pux + puy * puy + puz * puz;
-            a0s += jx + 1.5f * F;
+            a0s += jx + 0.5f * F;
             a1s += ex * ex + ey * ey + ez * ez;
             a2s += uu;
             umax2 = fmaxf(umax2, uu);

@@ -123,7 +123,7 @@ def test_forced_create_rejects_bad_arguments(lib):
     g = np.array([np.nan])
     assert lib.lbm_batch_create_forced(1, desc, g.ctypes.data, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
     g = np.array([1e-5])
-    t = lbm.make_options(collision=lbm.LBM_COLL_TRT)
+    t = lbm.make_options(collision=lbm.LBM_COLL_TRT, trt_lambda=-1.0)
     assert lib.lbm_batch_create_forced(1, desc, g.ctypes.data, C.byref(t), C.byref(h)) == lbm.LBM_ERR_ARG
     assert h.value is None
 

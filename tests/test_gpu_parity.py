@@ -544,3 +544,39 @@ def test_solve_sharded_without_a_process_group_runs_the_whole_list():
         lbm.lbm_run_to_steady(s, 1e-8, 200000)
         k2, _ = lbm.lbm_permeability(s)
     assert np.array_equal(k, k2) and np.all(st == 0)
+
+
+@pytest.mark.parametrize("eq", [0, 1])
+def test_forced_trt_steps_match_oracle(eq):
+    rng = np.random.default_rng(8)
+    tau, g, lam = 0.8, 2e-4, 3.0 / 16.0
+    tm = O.tau_minus(tau, lam)
+    opts = lbm.make_options(equilibrium=eq, collision=lbm.LBM_COLL_TRT, trt_lambda=lam)
+    for q, mask in _forced_masks():
+        with lbm.lbm_batch_create_forced([mask], [tau], [g], opts) as s:
+            f0 = lbm.lbm_get_populations(s, 0)
+            lbm.lbm_step(s, 5)
+            _assert_close(lbm.lbm_get_populations(s, 0), O.run_forced(mask, f0, tau, g, 5, eq, tau_m=tm), q, mask)
+            f = _w(q) * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
+            f[mask.astype(bool)] = 0
+            lbm.lbm_set_populations(s, 0, f)
+            start = lbm.lbm_get_populations(s, 0)
+            lbm.lbm_step(s, 1)
+            _assert_close(lbm.lbm_get_populations(s, 0), O.step_forced(mask, start, tau, g, eq, tau_m=tm), q, mask)
+
+
+def test_forced_channel_closed_forms_on_device():
+    """Force-driven channel on the GPU: BGK gives the pressure-driven exact
+    k = (h^2 - 1 + 8 (tau - 1/2)^2)/12, TRT with Lambda = 3/16 gives
+    (h^2 + 1/2)/12 for every tau."""
+    h, g = 8, 1e-6
+    m = np.zeros((h + 2, 6), np.uint8)
+    m[0] = m[-1] = 1
+    for tau in (0.7, 1.2):
+        for coll, expect in ((lbm.LBM_COLL_BGK, (h * h - 1 + 8 * (tau - 0.5) ** 2) / 12.0),
+                             (lbm.LBM_COLL_TRT, (h * h + 0.5) / 12.0)):
+            opts = lbm.make_options(equilibrium=lbm.LBM_EQ_LINEAR, collision=coll)
+            with lbm.lbm_batch_create_forced([m], [tau], [g], opts) as s:
+                lbm.lbm_run_to_steady(s, 1e-9, 400000)
+                k, _ = lbm.lbm_permeability(s)
+            assert k[0] * (h + 2) / h == pytest.approx(expect, rel=2e-4)

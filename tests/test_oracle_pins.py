@@ -734,11 +734,48 @@ def test_forced_step_without_force_equals_the_pressure_driven_bulk_step():
 
 def test_forced_eq2_velocity_is_the_half_step_velocity():
     """All-fluid periodic box from rest: the post-collision momentum after t
-    steps is t F, and Eq. 2 takes u = (j + F/2)/rho, so k = nu <u>/g is exactly
-    nu (t + 1/2)."""
+    steps is t F; the fluid momentum of Guo's scheme is the pre-collision
+    momentum (t - 1) F plus F/2, so k = nu <u>/g is exactly nu (t - 1/2)."""
     m = np.zeros((3, 4), np.uint8)
     tau, g = 0.9, 1e-5
     f = O.init(m, 1.0, 1.0)
     for t in range(1, 4):
         f = O.run_forced(m, f, tau, g, 1)
-        assert O.permeability_forced(m, f, tau, g) == pytest.approx((tau - 0.5) / 3.0 * (t + 0.5), rel=1e-10)
+        assert O.permeability_forced(m, f, tau, g) == pytest.approx((tau - 0.5) / 3.0 * (t - 0.5), rel=1e-10)
+
+
+@pytest.mark.parametrize("h", [6, 10])
+@pytest.mark.parametrize("tau", [0.6, 1.2])
+def test_forced_channel_closed_forms(h, tau):
+    """Force-driven channel between bounce-back walls (periodic in x), linear
+    equilibrium.  BGK reproduces the exact pressure-driven solution
+    k = (h^2 - 1 + 8 (tau - 1/2)^2)/12 (a body force and a uniform pressure
+    gradient drive the bulk alike).  TRT with Lambda = 3/16 gives the exact
+    parabola u = g y (h - y)/(2 nu) with the walls half way between nodes; its
+    mean over the h node rows is g (h^2 + 1/2)/(12 nu), so k = (h^2 + 1/2)/12
+    for every tau."""
+    g = 1e-6
+    m = np.zeros((h + 2, 4), np.uint8)
+    m[0] = m[-1] = 1
+    f, rc, _, _ = O.run_forced_to_steady(m, O.init(m, 1.0, 1.0), tau, g, 1e-12, 400000, eq=O.EQ_LINEAR)
+    assert rc == 0
+    k = O.permeability_forced(m, f, tau, g) * (h + 2) / h
+    assert k == pytest.approx((h * h - 1 + 8 * (tau - 0.5) ** 2) / 12.0, rel=1e-9)
+    tm = O.tau_minus(tau, 3.0 / 16.0)
+    f, rc, _, _ = O.run_forced_to_steady(m, O.init(m, 1.0, 1.0), tau, g, 1e-12, 400000, eq=O.EQ_LINEAR, tau_m=tm)
+    assert rc == 0
+    k = O.permeability_forced(m, f, tau, g) * (h + 2) / h
+    assert k == pytest.approx((h * h + 0.5) / 12.0, rel=1e-9)
+
+
+def test_forced_trt_with_equal_times_is_bgk():
+    rng = np.random.default_rng(23)
+    for q, shape in ((9, (7, 11)), (19, (4, 5, 9))):
+        mask = (rng.random(shape) < 0.2).astype(np.uint8)
+        w = O.lattice(q)[1]
+        f = w * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
+        f[mask.astype(bool)] = 0
+        for eq in (0, 1):
+            a = O.step_forced(mask, f, 0.8, 1e-3, eq)
+            b = O.step_forced(mask, f, 0.8, 1e-3, eq, tau_m=0.8)
+            assert np.abs(a - b).max() < 1e-15
