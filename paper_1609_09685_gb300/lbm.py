@@ -351,6 +351,33 @@ def lbm_local_knudsen(s: Solver, d: int):
     return d2.reshape(shape), h.reshape(shape), kn.reshape(shape)
 
 
+def lbm_status_string(status: int) -> str:
+    return load().lbm_status_string(int(status)).decode()
+
+
+def lbm_last_error(s: Optional["Solver"] = None) -> str:
+    """Detail of the last failure on this handle (None: this thread's last
+    failure outside a handle)."""
+    return load().lbm_last_error(s.handle if s is not None else None).decode(errors="replace")
+
+
+def lbm_options_default() -> lbm_options:
+    o = lbm_options()
+    load().lbm_options_default(C.byref(o))
+    return o
+
+
+def lbm_info(s: "Solver"):
+    """(number of domains, Q, total fluid nodes)."""
+    n, q, nf = C.c_int32(), C.c_int32(), C.c_int64()
+    _check(load().lbm_info(s.handle, C.byref(n), C.byref(q), C.byref(nf)), s.handle)
+    return n.value, q.value, nf.value
+
+
+def lbm_destroy(s: "Solver") -> None:
+    s.close()
+
+
 KERNEL_KINDS = ("gather", "local", "pull", "pull_observe")
 
 

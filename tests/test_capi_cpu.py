@@ -36,6 +36,13 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_every_declared_entry_point_has_a_binding_of_the_same_name():
+    missing = [n for n in sorted(_declared()) if not hasattr(lbm, n)]
+    assert missing == []
+    assert lbm.lbm_status_string(lbm.LBM_ERR_ARG) == "invalid argument"
+    assert lbm.lbm_options_default().k_tol == pytest.approx(1e-5)
+
+
 def test_binding_names_match_header():
     names = _declared()
     for n in ("lbm_qsgs", "lbm_create_domain", "lbm_create_domain_3d", "lbm_batch_create",
