@@ -32,6 +32,13 @@
  *   - Sec. 2 ("randomly generated quartet structure"): QSGS (Wang et al. 2007)
  *     growth of the solid phase driven by a counter-based splitmix64 hash
  *     (Steele, Lea & Flood 2014), with an exact target solid count.
+ *   - Sec. 2 (multi-relaxation models): the TRT collision (Ginzburg 2005).
+ *   - Sec. 2, Eq. (2): force-driven flow with every face periodic and the
+ *     forcing of Guo, Zheng & Shi (2002); k = nu <u> / g.
+ *   - Sec. 2 (local Knudsen number): brute-force distance to the nearest solid
+ *     node, pore size 2 D - 1.
+ * Every function is pinned by the CPU tests (closed forms, invariants,
+ * published values); only the paper-level figure curves are unpinned.
  */
 #include <math.h>
 #include <stdint.h>
