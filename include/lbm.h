@@ -222,7 +222,6 @@ lbm_status lbm_step(lbm_handle h, int64_t nsteps);
 lbm_status lbm_local_knudsen(lbm_handle h, int32_t d, uint32_t* d2_out, double* h_out, double* kn_out);
 
 /*
- * Measurement: advance nsteps plain steps exactly as lbm_step does/*
  * Measurement: advance nsteps plain steps exactly as lbm_step does (same
  * kernels, same pairing), but launch every kernel on its own with a CUDA event
  * recorded before and after it on the solver's stream, instead of through the
