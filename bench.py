@@ -5,11 +5,15 @@ One benchmark step is one convergence-check interval of the steady-state
 iteration over the whole workload: N-1 fused stream + boundary + collide
 steps, one more that also reduces the FP64 observables, the per-domain
 reduction, and the host readback that the steady-state control needs.  The
-default workload is the Sec. 2 relaxation-time sweep -- 3 resolutions (400x200,
-800x400, 1200x600 at porosities 0.7394 / 0.7532 / 0.7578) x 8 values of tau -
-1/2 -- run as one batch of 24 domains (8.96 M nodes, 0.32 GB per population
-copy, larger than L2).  The metric is MLUPS counted over fluid nodes (million
-fluid-node lattice updates per second), whole job over all ranks.
+default workload is the batch of 128 independent uneven D2Q9 domains (N_x
+uniform in [200, 1200], N_y = N_x/2, porosity U[0.6, 0.8], tau U[0.51, 1.5]; 23
+M fluid nodes, 1.7 GB of populations per step, 13x the L2), the largest 2D
+configuration of the paper's sweeps run as one batch.  The metric is MLUPS
+counted over fluid nodes (million fluid-node lattice updates per second),
+whole job over all ranks.  The same line carries the per-kernel rooflines of
+four 256x128x128 D3Q19 domains (`roofline_d3q19`) and the time to
+permeability of the 400x200 tau sweep, batched against one domain at a time,
+measured against the FP64 oracle's converged k where one is stored.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
@@ -43,7 +47,10 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
-    p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="sweep")
+    p.add_argument("--workload", choices=["sweep", "batch128", "d3q19", "d3q19_one", "small"], default="batch128")
+    p.add_argument("--no-d3q19", action="store_true",
+                   help="skip the per-kernel rooflines of the D3Q19 256x128x128 workload")
+    p.add_argument("--no-ttp", action="store_true", help="skip the time-to-permeability measurement")
     p.add_argument("--interval", type=int, default=100)
     p.add_argument("--kn-sweep", action="store_true",
                    help="also solve the 24 tau-sweep domains to steady state (BGK and TRT) and report k/k_int vs Kn")
@@ -56,8 +63,6 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--ttp", action="store_true",
-                   help="also measure time-to-permeability, batched vs plain (one domain at a time)")
     p.add_argument("--ttp-sizes", default="400x200",
                    help="resolutions of the tau sweep used for --ttp, e.g. 400x200,800x400")
     p.add_argument("--ttp-tol", type=float, default=1e-4)
@@ -220,18 +225,27 @@ def oracle_sample(wl, seconds: float):
 # ---------------------------------------------------------------------------
 # time-to-permeability
 # ---------------------------------------------------------------------------
-def time_to_k(t, k, tol):
-    """First host time after which k(t) stays within tol (relative) of the
-    run's converged value for every later check interval."""
-    if len(k) == 0:
-        return None
-    kf = k[-1]
-    bad = np.where(~(np.abs(k - kf) <= tol * abs(kf)))[0]
-    i = int(bad[-1]) + 1 if len(bad) else 0
-    return float(t[min(i, len(t) - 1)])
+GOLDEN_K = os.path.join(ROOT, "tests", "golden", "converged_k.txt")
+
+
+def oracle_k_table():
+    """Converged FP64 oracle permeabilities stored by
+    tests/golden/make_converged_k.py: {(nx, ny, nz, seed, tau): (k, bound)}."""
+    out = {}
+    if not os.path.exists(GOLDEN_K):
+        return out
+    with open(GOLDEN_K) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            t = line.split()
+            key = (int(t[1]), int(t[2]), int(t[3]), int(t[4]), round(float(t[6]), 12))
+            out[key] = (float(t[8]), float(t[9]))
+    return out
 
 
 def measure_ttp(args, lbm, sp):
+    from paper_1609_09685_gb300.warmstart import time_to_k
     sizes = []
     for tok in args.ttp_sizes.split(","):
         nx, ny = (int(v) for v in tok.lower().split("x"))
@@ -246,38 +260,50 @@ def measure_ttp(args, lbm, sp):
         masks.append(cache[key])
     taus = [d.tau for d in wl.domains]
     drhos = [d.drho for d in wl.domains]
+    table = oracle_k_table()
+    k_ref = [table.get((d.nx, d.ny, d.nz, d.seed, round(d.tau, 12)), (None, None))[0] for d in wl.domains]
+    have_ref = all(v is not None for v in k_ref)
     opts = lbm.make_options(stream=sp)
     out = {"workload": wl.name, "sizes": args.ttp_sizes, "domains": len(wl.domains), "tol_rel": args.ttp_tol,
-           "residual_tol": wl.tol, "k_reference": "each run's own converged k (r < tol or FP32 stall)"}
+           "residual_tol": wl.tol,
+           "k_reference": ("FP64 oracle's converged k (tests/golden/converged_k.txt)" if have_ref
+                           else "each run's own converged k (no stored oracle k for every domain)")}
+    ref = k_ref if have_ref else [None] * len(masks)
     # batched: all domains in one solver, converged ones retire
     s = lbm.lbm_batch_create(masks, taus, drhos, opts)
     t0 = time.perf_counter()
     rc, st, steps, res = lbm.lbm_run_to_steady(s, wl.tol, wl.max_steps)
     t_batch = time.perf_counter() - t0
     kb, _ = lbm.lbm_permeability(s)
-    ttp_b = [time_to_k(lbm.lbm_get_history(s, d)[3], lbm.lbm_get_history(s, d)[1], args.ttp_tol)
-             for d in range(len(masks))]
+    ttp_b = []
+    for d in range(len(masks)):
+        _, kk, _, tt = lbm.lbm_get_history(s, d)
+        ttp_b.append(time_to_k(tt, kk, args.ttp_tol, ref[d])[0])
     s.close()
     # plain: one domain at a time
-    ttp_p, t_plain, kp, steps_p = [], 0.0, [], []
+    ttp_p, t_plain, kp = [], 0.0, []
     for d in range(len(masks)):
         s1 = lbm.lbm_create_domain(masks[d], taus[d], drhos[d], opts)
         t0 = time.perf_counter()
-        _, st1, stp1, _ = lbm.lbm_run_to_steady(s1, wl.tol, wl.max_steps)
+        lbm.lbm_run_to_steady(s1, wl.tol, wl.max_steps)
         t_plain += time.perf_counter() - t0
-        hs = lbm.lbm_get_history(s1, 0)
-        ttp_p.append(time_to_k(hs[3], hs[1], args.ttp_tol))
+        _, kk, _, tt = lbm.lbm_get_history(s1, 0)
+        ttp_p.append(time_to_k(tt, kk, args.ttp_tol, ref[d])[0])
         kp.append(float(lbm.lbm_permeability(s1)[0][0]))
-        steps_p.append(int(stp1[0]))
         s1.close()
+    reached = all(v is not None for v in ttp_b + ttp_p)
     out.update({
-        "batched_time_to_k_s": max(ttp_b), "plain_time_to_k_s": float(sum(ttp_p)),
+        "all_reached_tol": reached,
+        "batched_time_to_k_s": max(ttp_b) if reached else None,
+        "plain_time_to_k_s": float(sum(ttp_p)) if reached else None,
         "batched_stop_s": t_batch, "plain_stop_s": t_plain,
-        "speedup_time_to_k": float(sum(ttp_p)) / max(ttp_b),
+        "speedup_time_to_k": float(sum(ttp_p)) / max(ttp_b) if reached else None,
         "max_rel_k_diff_batched_vs_plain": float(np.max(np.abs(np.array(kb) - np.array(kp)) / np.abs(kp))),
+        "max_rel_k_diff_vs_oracle": (float(np.max(np.abs(np.array(kb) - np.array(k_ref)) / np.abs(k_ref)))
+                                     if have_ref else None),
         "per_domain": [{"tau": taus[d], "nx": wl.domains[d].nx, "steps": int(steps[d]),
-                        "status": int(st[d]), "k": float(kb[d]), "ttp_batched_s": ttp_b[d],
-                        "ttp_plain_s": ttp_p[d]} for d in range(len(masks))],
+                        "status": int(st[d]), "k": float(kb[d]), "k_oracle": k_ref[d],
+                        "ttp_batched_s": ttp_b[d], "ttp_plain_s": ttp_p[d]} for d in range(len(masks))],
     })
     return out
 
@@ -308,10 +334,12 @@ def measure_warmstart(args, lbm, sp):
         s1 = lbm.lbm_create_domain(ev.masks_host[d], ev.taus[d], ev.drhos[d], lbm.make_options())
         lbm.lbm_run_to_steady(s1, 1e-9, 400_000)
         stp, kk, rr, tt = lbm.lbm_get_history(s1, 0)
+        s1.close()
         tk, ik = WS.time_to_k(tt, kk, args.ttp_tol)
+        if tk is None:
+            continue
         plain_t.append(tk)
         plain_steps.append(int(stp[ik]))
-        s1.close()
     return {
         "shape": [ny, nx], "domains_compared": len(both), "domains_not_converged": res["domains_not_converged"], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
         "unet_params": int(net.nparams), "epochs": args.ws_epochs, "loss_first_last": [hist[0], hist[-1]],
@@ -430,6 +458,113 @@ def run_reference(args):
     return 0
 
 
+KERNEL_NAMES = {"gather": "k_aa_gather (gather step of the in-place pair)",
+                "local": "k_aa_local (local step of the in-place pair)",
+                "pull": "k_stream_collide (pull step)"}
+
+
+def masks_of(lbm, wl, sp):
+    cache, masks = {}, []
+    for d in wl.domains:
+        key = (d.shape, d.seed, d.porosity)
+        if key not in cache:
+            cache[key], _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity, d.d_face, stream=sp)
+        masks.append(cache[key])
+    return masks
+
+
+def time_intervals(lbm, s, stream, N, steps, warmup, barrier, sampler=None):
+    """W warm-up intervals, then K timed intervals (graph-launched), then the
+    same K intervals once more with every plain-step kernel bracketed by CUDA
+    events (lbm_profile_steps).  Returns (seconds of the timed region, seconds
+    per graph-launched plain step, seconds of the per-kernel pass,
+    {kind: [us, launches]}, clocks)."""
+    import torch
+    clocks = None
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lbm.lbm_step(s, N - 1)
+            lbm.lbm_step_observe(s, 1)
+        barrier()
+        if sampler is not None:
+            sampler.start()
+            time.sleep(0.4)
+        ka = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        kb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            ka[k].record(stream)
+            lbm.lbm_step(s, N - 1)
+            kb[k].record(stream)
+            lbm.lbm_step_observe(s, 1)
+        e1.record(stream)
+        barrier()
+        if sampler is not None:
+            clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    t_kern = sum(a.elapsed_time(b) for a, b in zip(ka, kb)) / 1e3 / (steps * (N - 1))
+    with torch.cuda.stream(stream):
+        barrier()
+        kt = {k: [0.0, 0] for k in lbm.KERNEL_KINDS}
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for k in range(steps):
+            prof = lbm.lbm_profile_steps(s, N - 1)
+            for kind, (us, cnt) in prof.items():
+                kt[kind][0] += us
+                kt[kind][1] += cnt
+            lbm.lbm_step_observe(s, 1)
+        p1.record(stream)
+        barrier()
+    t_prof = p0.elapsed_time(p1) / 1e3
+    return t, t_kern, t_prof, kt, clocks
+
+
+def kernel_table(kt, steps, bytes_per_launch, peak, workload, q):
+    """Per-kernel rooflines: algorithmic bytes per launch over the average
+    event-timed launch duration, and each kernel's share of plain-step time."""
+    kernels = {}
+    for kind in [k for k in kt if kt[k][1] > 0]:
+        us = kt[kind][0] / kt[kind][1]
+        a = bytes_per_launch / (us * 1e-6) / 1e9
+        kernels[kind] = {"kernel": KERNEL_NAMES.get(kind, kind), "launches_per_interval": kt[kind][1] // steps,
+                         "avg_launch_us": us, "achieved": a, "frac": a / peak,
+                         "traffic": profiled_traffic(workload, q, kind)}
+    total_us = sum(v["avg_launch_us"] * v["launches_per_interval"] for v in kernels.values())
+    for v in kernels.values():
+        v["share_of_plain_steps"] = v["avg_launch_us"] * v["launches_per_interval"] / total_us
+    return kernels
+
+
+def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak, peak_src):
+    """Per-kernel rooflines of a second workload, timed like the headline one
+    (used for the D3Q19 256x128x128 configuration)."""
+    wl = get_workload(wl_name, 0)
+    q = lattice_q(wl)
+    masks = masks_of(lbm, wl, sp)
+    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll)
+    s = lbm.lbm_batch_create(masks, [d.tau for d in wl.domains], [d.drho for d in wl.domains], opts)
+    fluid = s.fluid_nodes
+    bpl = 2 * 4 * q * fluid
+    t, t_kern, _, kt, _ = time_intervals(lbm, s, stream, N, steps, warmup, barrier)
+    s.close()
+    kernels = kernel_table(kt, steps, bpl, peak, wl_name, q)
+    dom_kind = max(kernels, key=lambda k: kernels[k]["share_of_plain_steps"])
+    dk = kernels[dom_kind]
+    ach = bpl / t_kern / 1e9
+    return {"workload": wl.name, "domains": len(wl.domains), "lattice": "D3Q19" if q == 19 else "D2Q9",
+            "fluid_nodes": fluid, "nodes": wl.cells, "mlups": steps * N * fluid / t / 1e6,
+            "bound": "hbm", "achieved": dk["achieved"], "peak": peak, "unit": "GB/s", "frac": dk["frac"],
+            "traffic": dk["traffic"], "kernel": dk["kernel"], "bytes_per_launch": bpl,
+            "algorithmic_bytes": f"{2 * 4 * q} B per fluid-node update (one step)",
+            "avg_launch_us": dk["avg_launch_us"], "peak_source": peak_src, "kernels": kernels,
+            "plain_step_average": {"avg_step_us": t_kern * 1e6, "achieved": ach, "frac": ach / peak,
+                                   "timing": "CUDA events around the graph-launched plain steps"}}
+
+
 def run_native(args):
     import torch
 
@@ -452,14 +587,7 @@ def run_native(args):
     N = args.interval
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-
-    masks_cache = {}
-    masks = []
-    for d in wl.domains:
-        key = (d.shape, d.seed, d.porosity)
-        if key not in masks_cache:
-            masks_cache[key], _ = lbm.lbm_qsgs(d.seed, d.shape, d.core_p, d.porosity, d.d_face, stream=sp)
-        masks.append(masks_cache[key])
+    masks = masks_of(lbm, wl, sp)
     taus = [d.tau for d in wl.domains]
     drhos = [d.drho for d in wl.domains]
     coll = lbm.LBM_COLL_TRT if args.collision == "trt" else lbm.LBM_COLL_BGK
@@ -473,52 +601,14 @@ def run_native(args):
         if dist is not None:
             dist.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            lbm.lbm_step(s, N - 1)
-            lbm.lbm_step_observe(s, 1)
-        barrier()
-        sampler = ClockSampler(local)
-        sampler.start()
-        time.sleep(0.4)
-        ka = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(args.steps):
-            ka[k].record(stream)
-            lbm.lbm_step(s, N - 1)
-            kb[k].record(stream)
-            lbm.lbm_step_observe(s, 1)
-        e1.record(stream)
-        barrier()
-        clocks = sampler.stop()
-    t = e0.elapsed_time(e1) / 1e3
-    t_kern = sum(a.elapsed_time(b) for a, b in zip(ka, kb)) / 1e3 / (args.steps * (N - 1))
-
-    # Per-kernel device times: the same K intervals once more, with the plain
-    # steps launched one by one between CUDA events on the solver's stream
-    # (lbm_profile_steps) instead of through the cached graph.
-    with torch.cuda.stream(stream):
-        barrier()
-        kt = {k: [0.0, 0] for k in lbm.KERNEL_KINDS}
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for k in range(args.steps):
-            prof = lbm.lbm_profile_steps(s, N - 1)
-            for kind, (us, cnt) in prof.items():
-                kt[kind][0] += us
-                kt[kind][1] += cnt
-            lbm.lbm_step_observe(s, 1)
-        p1.record(stream)
-        barrier()
-    t_prof = p0.elapsed_time(p1) / 1e3
+    t, t_kern, t_prof, kt, clocks = time_intervals(lbm, s, stream, N, args.steps, args.warmup, barrier,
+                                                    sampler=ClockSampler(local))
     kinds = [k for k in lbm.KERNEL_KINDS if kt[k][1] > 0]
     avg_us = [kt[k][0] / kt[k][1] for k in kinds]
     (t, t_kern, t_prof, *avg_us), (updates,) = combine_ranks(
         dist, "cuda", [t, t_kern, t_prof] + avg_us, [float(args.steps * N * fluid)])
+    for k, us in zip(kinds, avg_us):  # the slowest rank's kernel times
+        kt[k][0] = us * kt[k][1]
     value = updates / t / 1e6
 
     # end to end through the C ABI: host masks (pinned) -> create -> one interval
@@ -558,26 +648,19 @@ def run_native(args):
                "max_local_kn_over_domain_kn": max(
                    km / (np.sqrt(np.pi / 6) * (d.tau - 0.5) / d.nx) for km, d in zip(kmax, wl.domains))}
     s.close()
-    ttp = measure_ttp(args, lbm, sp) if (args.ttp and rank == 0) else None
+    peak, peak_src = measured_hbm_peak()
+    roof3 = None
+    if rank == 0 and not args.no_d3q19 and q == 9:
+        roof3 = roofline_of(lbm, "d3q19", sp, stream, N, args.steps, args.warmup, coll, torch.cuda.synchronize,
+                            peak, peak_src)
+    ttp = measure_ttp(args, lbm, sp) if (not args.no_ttp and rank == 0) else None
     f3d = measure_forced3d(lbm, sp) if (args.forced3d and rank == 0) else None
     kns = measure_kn_sweep(lbm, sp) if (args.kn_sweep and rank == 0) else None
     ws = measure_warmstart(args, lbm, sp) if (args.warmstart and rank == 0) else None
 
     if rank == 0:
-        peak, peak_src = measured_hbm_peak()
         achieved_step = bytes_per_launch / t_kern / 1e9
-        names = {"gather": "k_aa_gather (gather step of the in-place pair)",
-                 "local": "k_aa_local (local step of the in-place pair)",
-                 "pull": "k_stream_collide (pull step)"}
-        kernels = {}
-        for kind, us in zip(kinds, avg_us):
-            a = bytes_per_launch / (us * 1e-6) / 1e9
-            kernels[kind] = {"kernel": names.get(kind, kind), "launches_per_interval": kt[kind][1] // args.steps,
-                             "avg_launch_us": us, "achieved": a, "frac": a / peak,
-                             "traffic": profiled_traffic(args.workload, q, kind)}
-        total_us = sum(v["avg_launch_us"] * v["launches_per_interval"] for v in kernels.values())
-        for v in kernels.values():
-            v["share_of_plain_steps"] = v["avg_launch_us"] * v["launches_per_interval"] / total_us
+        kernels = kernel_table(kt, args.steps, bytes_per_launch, peak, args.workload, q)
         dom_kind = max(kernels, key=lambda k: kernels[k]["share_of_plain_steps"])
         dk = kernels[dom_kind]
         cpu = None
@@ -618,6 +701,8 @@ def run_native(args):
             "ms_per_step_per_kernel_pass": t_prof / args.steps * 1e3,
             "clocks": clocks,
         }
+        if roof3 is not None:
+            line["roofline_d3q19"] = roof3
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if ttp is not None:

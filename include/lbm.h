@@ -111,6 +111,16 @@ const char* lbm_status_string(lbm_status s);
 const char* lbm_last_error(lbm_handle h);
 /* Defaults described in lbm_options. */
 void lbm_options_default(lbm_options* opt);
+/*
+ * The lattice tables the kernels use (Qian, d'Humieres & Lallemand 1992; the
+ * direction order above): for q = 9 (D2Q9) or 19 (D3Q19), c[3 q] the
+ * velocities (x, y, z per direction), w[q] the weights, opp[q] the reversed
+ * direction, flip_y[q] / flip_z[q] the direction with its y / z component
+ * reversed (the specular reflection at the symmetry planes, Sec. 2 Fig. 1).
+ * Host arrays, each nullable.  Host only; no device is touched.
+ * LBM_ERR_ARG for any other q.
+ */
+lbm_status lbm_lattice(int32_t q, int32_t* c, double* w, int32_t* opp, int32_t* flip_y, int32_t* flip_z);
 
 /*
  * QSGS porous mask (Sec. 2, "randomly generated quartet structure"; QSGS
@@ -123,7 +133,9 @@ void lbm_options_default(lbm_options* opt);
  * iteration broken by ascending (draw, cell index)).  nz = 1 gives a 2D mask.
  * mask_out: host, nx*ny*nz bytes.  iterations (nullable): growth iterations.
  * Errors: LBM_ERR_ARG for bad sizes / porosity outside [0,1] / more than 2^31
- * cells; LBM_ERR_INTERNAL if no solid core appears while S > 0.
+ * cells; LBM_ERR_INTERNAL if no solid core appears while S > 0, or if 10^6
+ * growth iterations pass before S cells are solid (each with its own detail
+ * string).
  */
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p,
                     double porosity, double d_face, void* stream, uint8_t* mask_out,
@@ -145,6 +157,8 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
  *   - The first call on a device looks up the scratch array's device address
  *     (once per device, with that device current); make that first call before
  *     any stream capture.
+ *   - Every call, the first and the later ones, synchronises `stream` and reads
+ *     a candidate counter back to the host between its kernel launches.
  *   - All calls share the scratch array and it keeps the last call's contents
  *     (every value a call reads is written by that call first).  Calls that
  *     overlap on the GPU -- from several host threads or several streams --
@@ -191,6 +205,22 @@ lbm_status lbm_create_domain(const uint8_t* mask, int32_t nx, int32_t ny, double
 lbm_status lbm_create_domain_3d(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz,
                                 double tau, double drho, const lbm_options* opt,
                                 lbm_handle* out);
+/*
+ * Batch names of the three calls that act on a whole batch.  Every solver is a
+ * batch (a single domain is a batch of one), so lbm_batch is the same handle
+ * and these are the batch forms of the calls below:
+ *   lbm_batch_run_to_steady: lbm_run_to_steady (Sec. 2, "iterated to steady
+ *     state") with only the per-domain statuses (host array of n, nullable);
+ *   lbm_batch_permeability: lbm_permeability (Sec. 2, Darcy's law with the
+ *     simulated mass flow rate; nu from Eq. 1) without the Kn output;
+ *   lbm_batch_destroy: lbm_destroy.
+ * Statuses and errors are those of the calls they stand for.
+ */
+typedef lbm_handle lbm_batch;
+lbm_status lbm_batch_run_to_steady(lbm_batch b, double tol, int64_t max_steps, lbm_status* per_domain);
+lbm_status lbm_batch_permeability(lbm_batch b, double* k);
+void lbm_batch_destroy(lbm_batch b);
+
 /* Synchronises the solver's stream and frees its resources.  Device memory of
  * solvers comes from one stream-ordered pool per device; up to 8 GB of freed
  * blocks stay cached there for the next solver, the rest returns to the

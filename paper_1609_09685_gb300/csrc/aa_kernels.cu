@@ -3,6 +3,7 @@
 // inlet/outlet bits the local step reads.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <utility>
 
 #include "lbm_launch.h"
@@ -431,12 +432,17 @@ static cudaError_t aa_half_launch(int half, int threads, const HotArgs& A, cudaS
         else kern = k_aa_gather3<L, EQ>;
         const size_t sm = gather_smem_bytes<L>(threads);
         if (GatherSmem<L>::on) {
-            static bool attr_set = false;  // per template instance
-            if (!attr_set) {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)gather_smem_bytes<L>(256));
+            // a function attribute is per device: set it once on each
+            static std::atomic<uint64_t> attr_set{0};  // bit d: set on device d (per template instance)
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return e;
+            const uint64_t bit = 1ull << (dev & 63);
+            if (dev >= 64 || !(attr_set.load() & bit)) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gather_smem_bytes<L>(256));
                 if (e != cudaSuccess) return e;
-                attr_set = true;
+                if (dev < 64) attr_set.fetch_or(bit);
             }
         }
         kern<<<nb, threads, sm, st>>>(A);

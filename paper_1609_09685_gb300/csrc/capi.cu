@@ -46,6 +46,7 @@ struct DomainHost {
     int32_t k_dead = 0;       // consecutive checks with |k| below 0.1 k_tol of its peak
     double k_peak = 0.0;      // largest |k| seen in this run
     bool has_obs = false;
+    bool forced_state = false;  // populations are the post-collision state of a forced step
     double obs[kNumObs] = {0};
     // per check interval of the last lbm_run_to_steady: step, k, residual,
     // host seconds since the call began
@@ -334,9 +335,18 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     return LBM_OK;
 }
 
+// After n > 0 steps of a force-driven solver, the active domains hold the
+// post-collision state of a forced step.
+void mark_forced_state(lbm_handle h, int64_t n) {
+    if (!h->forced || n <= 0) return;
+    for (auto& D : h->dom)
+        if (D.active) D.forced_state = true;
+}
+
 // Same work through a cached CUDA graph (one per step count, observe flag and
 // starting buffer parity).
 lbm_status run_steps(lbm_handle h, int64_t n, bool obs) {
+    mark_forced_state(h, n);
     if (!h->opt.use_graphs || n <= 1 || h->st == nullptr) return enqueue_steps(h, n, obs);
     GraphKey key{n, obs ? 1 : 0, h->cur};
     auto it = h->graphs.find(key);
@@ -369,10 +379,15 @@ void store_obs(lbm_handle h) {
         std::memcpy(h->dom[d].obs, h->h_obs + d * kNumObs, sizeof(double) * kNumObs);
         // An observation without a step comes from the pressure-driven observe
         // kernel (slot 0 = link flux).  For force-driven solvers slot 0 must be
-        // the Eq. 2 flux: the fluid momentum of Guo's scheme is the stored
-        // post-collision momentum (slot 6) minus F/2 per fluid node.
+        // the Eq. 2 flux: when the populations come from a forced step, the
+        // fluid momentum of Guo's scheme is the stored post-collision momentum
+        // (slot 6) minus F/2 per fluid node; a state that no forced step has
+        // produced yet (fresh, or set by the caller) holds its fluid momentum
+        // as it is.
         if (h->forced && h->obs_only)
-            h->dom[d].obs[0] = h->dom[d].obs[6] - 0.5 * h->dom[d].g * h->opt.rho_out * h->dom[d].fluid_count;
+            h->dom[d].obs[0] = h->dom[d].obs[6] - (h->dom[d].forced_state ? 0.5 * h->dom[d].g * h->opt.rho_out *
+                                                                         h->dom[d].fluid_count
+                                                                   : 0.0);
         h->dom[d].has_obs = true;
     }
 }
@@ -472,6 +487,31 @@ const char* lbm_status_string(lbm_status s) {
 
 const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : t_err.c_str(); }
 
+}  // extern "C"
+
+namespace {
+template <class L>
+void lattice_tables(int32_t* c, double* w, int32_t* o, int32_t* fy, int32_t* fz) {
+    for (int i = 0; i < L::Q; ++i) {
+        if (c)
+            for (int a = 0; a < 3; ++a) c[3 * i + a] = L::c(i, a);
+        if (w) w[i] = L::wd(i);
+        if (o) o[i] = opp<L>(i);
+        if (fy) fy[i] = flip<L>(i, true, false);
+        if (fz) fz[i] = flip<L>(i, false, true);
+    }
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_lattice(int32_t q, int32_t* c, double* w, int32_t* opp_out, int32_t* flip_y, int32_t* flip_z) {
+    if (q == 9) lattice_tables<D2Q9>(c, w, opp_out, flip_y, flip_z);
+    else if (q == 19) lattice_tables<D3Q19>(c, w, opp_out, flip_y, flip_z);
+    else return fail(nullptr, LBM_ERR_ARG, "q must be 9 (D2Q9) or 19 (D3Q19)");
+    return LBM_OK;
+}
+
 void lbm_options_default(lbm_options* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
@@ -519,6 +559,7 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
         if (r == -2) rs = cuda_fail(nullptr, ce, "qsgs kernels");
         else if (r == -1) rs = fail(nullptr, LBM_ERR_ARG, "bad qsgs arguments");
         else if (r == -3) rs = fail(nullptr, LBM_ERR_INTERNAL, "no solid core to grow from");
+        else if (r == -4) rs = fail(nullptr, LBM_ERR_INTERNAL, "growth iteration cap reached before the target porosity");
         else {
             e = cudaMemcpyAsync(mask_out, d_mask, N, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -860,6 +901,7 @@ lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int
     }
     if (nsteps == 0) return LBM_OK;
     KernelProf prof;
+    mark_forced_state(h, nsteps);
     lbm_status s = enqueue_steps(h, nsteps, false, &prof);
     if (s != LBM_OK) return s;
     CK(h, cudaStreamSynchronize(h->st));
@@ -1000,6 +1042,14 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
     return LBM_OK;
 }
 
+lbm_status lbm_batch_run_to_steady(lbm_batch b, double tol, int64_t max_steps, lbm_status* per_domain) {
+    return lbm_run_to_steady(b, tol, max_steps, per_domain, nullptr, nullptr);
+}
+
+lbm_status lbm_batch_permeability(lbm_batch b, double* k) { return lbm_permeability(b, k, nullptr); }
+
+void lbm_batch_destroy(lbm_batch b) { lbm_destroy(b); }
+
 lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (!k) return fail(h, LBM_ERR_ARG, "k is null");
@@ -1082,6 +1132,7 @@ lbm_status lbm_set_populations(lbm_handle h, int32_t d, const double* f) {
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_populations");
     h->dom[d].has_obs = false;
+    h->dom[d].forced_state = false;
     return LBM_OK;
 }
 
@@ -1114,6 +1165,7 @@ lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const floa
     cudaFree(buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
     h->dom[d].has_obs = false;
+    h->dom[d].forced_state = false;
     return LBM_OK;
 }
 

@@ -58,7 +58,11 @@ struct QsgsScratch {
     unsigned long long* counter;
     unsigned long long* host_counter;  // pinned
 };
-// Returns 0 on success, -1 argument error, -3 no cores, -2 CUDA error (cuda_err set).
+// Growth iterations after which qsgs_generate gives up (the solid count has
+// stopped growing, e.g. every remaining fluid cell is out of reach).
+constexpr int kMaxGrowthIterations = 1000000;
+// Returns 0 on success, -1 argument error, -2 CUDA error (cuda_err set),
+// -3 no solid core to grow from, -4 kMaxGrowthIterations reached.
 int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double porosity,
                   double d_face, uint8_t* d_mask, const QsgsScratch& sc, cudaStream_t st,
                   int* iterations, cudaError_t* cuda_err);

@@ -194,7 +194,7 @@ int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double p
     while (count < S) {
         if (count == 0) return -3;
         ++t;
-        if (t > 1000000) return -3;
+        if (t > kMaxGrowthIterations) return -4;
         QCK(cudaMemcpyAsync(sc.start, d_mask, N, cudaMemcpyDeviceToDevice, st));
         QCK(cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st));
         k_grow<<<grid_for(N), 256, 0, st>>>(sm_out(seed, (uint64_t)t + 1), nx, ny, nz, sl, sc.start, sc.keys,

@@ -88,6 +88,7 @@ lbm_status lbm_qsgs_noalloc(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, d
     if (r == -2) return noalloc_fail(LBM_ERR_CUDA, std::string("qsgs kernels: ") + cudaGetErrorString(ce));
     if (r == -1) return noalloc_fail(LBM_ERR_ARG, "bad qsgs arguments");
     if (r == -3) return noalloc_fail(LBM_ERR_INTERNAL, "no solid core to grow from");
+    if (r == -4) return noalloc_fail(LBM_ERR_INTERNAL, "growth iteration cap reached before the target porosity");
     if (iterations) *iterations = it;
     return LBM_OK;
 }

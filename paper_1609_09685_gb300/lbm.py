@@ -113,6 +113,10 @@ def load(path: Optional[str] = None):
         "lbm_local_knudsen": (i32, [P, i32, P, P, P]),
         "lbm_run_to_steady": (i32, [P, d, i64, P, P, P]),
         "lbm_permeability": (i32, [P, P, P]),
+        "lbm_batch_run_to_steady": (i32, [P, d, i64, P]),
+        "lbm_batch_permeability": (i32, [P, P]),
+        "lbm_batch_destroy": (None, [P]),
+        "lbm_lattice": (i32, [i32, P, P, P, P, P]),
         "lbm_get_fields": (i32, [P, i32, P, P, P, P]),
         "lbm_get_populations": (i32, [P, i32, P]),
         "lbm_set_populations": (i32, [P, i32, P]),
@@ -407,6 +411,38 @@ def lbm_permeability(s: Solver):
     kn = np.zeros(s.n_domains, np.float64)
     _check(load().lbm_permeability(s.handle, _ptr(k), _ptr(kn)), s.handle)
     return k, kn
+
+
+def lbm_batch_run_to_steady(s: Solver, tol: float, max_steps: int):
+    """Returns (overall status, per-domain status)."""
+    st = np.zeros(s.n_domains, np.int32)
+    rc = _check(load().lbm_batch_run_to_steady(s.handle, tol, int(max_steps), _ptr(st)), s.handle)
+    return rc, st
+
+
+def lbm_batch_permeability(s: Solver) -> np.ndarray:
+    """k[n] from the last observation."""
+    k = np.zeros(s.n_domains, np.float64)
+    _check(load().lbm_batch_permeability(s.handle, _ptr(k)), s.handle)
+    return k
+
+
+def lbm_batch_destroy(s: Solver) -> None:
+    """Frees the batch through lbm_batch_destroy; the Solver is closed after."""
+    if s._h:
+        load().lbm_batch_destroy(s._h)
+        s._h = None
+
+
+def lbm_lattice(q: int):
+    """(c[q, 3], w[q], opp[q], flip_y[q], flip_z[q]): the kernels' lattice tables."""
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q, np.float64)
+    o = np.zeros(q, np.int32)
+    fy = np.zeros(q, np.int32)
+    fz = np.zeros(q, np.int32)
+    _check(load().lbm_lattice(int(q), _ptr(c), _ptr(w), _ptr(o), _ptr(fy), _ptr(fz)))
+    return c, w, o, fy, fz
 
 
 def _shape(s: Solver, d: int):

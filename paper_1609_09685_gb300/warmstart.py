@@ -324,13 +324,19 @@ def predict(net: UNet, ds: Dataset, i0: int, n: int):
     return net.forward(ds.inputs[i0:i0 + n], n, ds.h, ds.w)
 
 
-def time_to_k(t, k, tol):
+def time_to_k(t, k, tol, k_ref=None):
+    """(time, index) of the first check interval after which k(t) stays within
+    tol (relative) of k_ref for every later interval; k_ref is the oracle's
+    converged k where one is known, else the run's own last k.  (None, None)
+    when the history is empty or its last k is not within tol of k_ref."""
+    k = np.asarray(k, np.float64)
     if len(k) == 0:
         return None, None
-    kf = k[-1]
+    kf = k[-1] if k_ref is None else float(k_ref)
     bad = np.where(~(np.abs(k - kf) <= tol * abs(kf)))[0]
     i = int(bad[-1]) + 1 if len(bad) else 0
-    i = min(i, len(t) - 1)
+    if i >= len(k):
+        return None, None
     return float(t[i]), i
 
 

@@ -10,30 +10,44 @@ into R_i(x) and the local step reads each node's own slots, which is the
 arithmetic of two pull steps exactly when
   (1) no slot is read twice, and
   (2) R_i(x) = (y, opp j)  <=>  R_j(y) = (x, opp i).
-The map is built here from those rules in plain Python and the two properties
-are checked on random masks in 2D and 3D."""
+The map is built here in plain Python from those rules, with the direction
+tables the kernels themselves use (velocities, opposite and y/z-mirrored
+directions, exported by lbm_lattice), and the two properties are checked on
+random masks in 2D and 3D.  What stays outside this check is the kernels'
+index arithmetic (windows, popcounts, slot offsets); the GPU parity tests of
+pairs against pull steps and the oracle cover that."""
 import numpy as np
 import pytest
 
 import oracle as O
+from paper_1609_09685_gb300 import build, lbm
 
 
-def _read_map(mask, c, opp):
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    lbm.load()
+
+
+def _tables(q):
+    """Direction tables of the kernels; checked against the oracle's own."""
+    c, w, opp, fy, fz = lbm.lbm_lattice(q)
+    co, wo, oo = O.lattice(q)
+    assert np.array_equal(c, co) and np.array_equal(w, wo) and np.array_equal(opp, oo)
+    return c, opp, fy, fz
+
+
+def _read_map(mask, c, opp, fy_tab, fz_tab):
     q = len(c)
-    shape = mask.shape
     if mask.ndim == 2:
         mask = mask[None]
     nz, ny, nx = mask.shape
     flip = {}
     for i in range(q):
-        for fy in (False, True):
-            for fz in (False, True):
-                v = np.array(c[i])
-                if fy:
-                    v[1] = -v[1]
-                if fz:
-                    v[2] = -v[2]
-                flip[i, fy, fz] = int(np.where((c == v).all(axis=1))[0][0])
+        flip[i, False, False] = i
+        flip[i, True, False] = int(fy_tab[i])
+        flip[i, False, True] = int(fz_tab[i])
+        flip[i, True, True] = int(fz_tab[fy_tab[i]])
     R = {}
     for z in range(nz):
         for y in range(ny):
@@ -62,13 +76,11 @@ def _read_map(mask, c, opp):
 def test_read_map_is_injective_and_paired(dim):
     rng = np.random.default_rng(5 + dim)
     q = 9 if dim == 2 else 19
-    c, _, opp = O.lattice(q)
-    c = [tuple(int(v) for v in row) for row in c]
-    c = np.array(c)
+    c, opp, fy, fz = _tables(q)
     for trial in range(3):
         shape = (9, 13) if dim == 2 else (4, 5, 7)
         mask = (rng.random(shape) < 0.3).astype(np.uint8)
-        R = _read_map(mask, c, opp)
+        R = _read_map(mask, c, opp, fy, fz)
         # (1) injective
         assert len(set(R.values())) == len(R)
         # (2) pairing
@@ -80,10 +92,9 @@ def test_read_map_is_injective_and_paired(dim):
 def test_pairing_breaks_for_a_wrong_mirror_rule():
     """The check has teeth: mirroring without flipping the direction (a
     plausible mistake) violates the pairing."""
-    c, _, opp = O.lattice(9)
-    c = np.array(c)
+    c, opp, fy, fz = _tables(9)
     mask = np.zeros((4, 6), np.uint8)
-    R = _read_map(mask, c, opp)
+    R = _read_map(mask, c, opp, fy, fz)
     bad = dict(R)
     # replace the mirror at the top row by a non-flipping one
     for (x, i), (y, k) in R.items():

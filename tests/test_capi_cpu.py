@@ -145,3 +145,47 @@ def test_trt_options_are_validated(lib):
 
 def test_local_knudsen_rejects_null_handle(lib):
     assert lib.lbm_local_knudsen(None, 0, None, None, None) == lbm.LBM_ERR_ARG
+
+
+def test_batch_calls_reject_a_null_batch(lib):
+    st = np.zeros(1, np.int32)
+    k = np.zeros(1)
+    assert lib.lbm_batch_run_to_steady(None, 1e-9, 10, st.ctypes.data) == lbm.LBM_ERR_ARG
+    assert lib.lbm_batch_permeability(None, k.ctypes.data) == lbm.LBM_ERR_ARG
+    lib.lbm_batch_destroy(None)  # a no-op, like lbm_destroy(NULL)
+
+
+def test_lattice_tables(lib):
+    """The kernels' direction tables: opposite and mirrored directions are
+    involutions with the right velocities, and the weights make the second
+    moment isotropic with c_s^2 = 1/3."""
+    for q in (9, 19):
+        c, w, opp, fy, fz = lbm.lbm_lattice(q)
+        assert c.shape == (q, 3) and abs(w.sum() - 1.0) < 1e-15
+        assert np.array_equal(c[opp], -c) and np.array_equal(opp[opp], np.arange(q))
+        assert np.array_equal(c[fy], c * [1, -1, 1]) and np.array_equal(c[fz], c * [1, 1, -1])
+        second = np.einsum("i,ia,ib->ab", w, c, c)
+        d = 2 if q == 9 else 3
+        assert np.allclose(second[:d, :d], np.eye(d) / 3.0, atol=1e-15)
+    out = np.zeros(57, np.int32)
+    assert lib.lbm_lattice(7, out.ctypes.data, None, None, None, None) == lbm.LBM_ERR_ARG
+
+
+def test_readme_c_example_compiles(lib, tmp_path):
+    """The C example of the README compiles against include/lbm.h and links
+    against the library (it is not run: it needs a GPU)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    txt = open(os.path.join(ROOT, "README.md")).read()
+    m = re.search(r"```c\n(.*?)```", txt, flags=re.S)
+    assert m, "README has no C example"
+    src = tmp_path / "example.c"
+    src.write_text(m.group(1))
+    libdir = os.path.dirname(lbm.library_path())
+    r = subprocess.run([cc, "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(tmp_path / "example"), "-L", libdir, "-llbm_gb300", f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

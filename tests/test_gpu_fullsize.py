@@ -1,5 +1,5 @@
 """Parity at the full benchmark sizes, in the launch configuration bench.py
-times (the default options: 256-thread blocks, 8-row strips, graphs).
+times (the default options: 128-thread blocks, 8-row strips, graphs).
 
 At these sizes the oracle cannot run to steady state within a test, so the
 check is one-step consistency on sampled domains: after the GPU has advanced

@@ -536,6 +536,48 @@ def test_forced_observation_without_stepping_gives_eq2_flux():
         assert k[0] == pytest.approx(O.permeability_forced(mask, f, tau, g), rel=1e-5)
 
 
+def test_forced_permeability_of_states_no_forced_step_produced():
+    """The F/2 of Eq. 2's Guo momentum belongs to post-collision states of a
+    forced step only: a fresh force-driven solver (fluid at rest) reports
+    k = 0, and populations set by the caller report their own momentum; after
+    a forced step the oracle's Eq. 2 applies again."""
+    mask, _ = O.qsgs((6, 8, 20), 3, 0.05, 0.75)
+    tau, g = 0.9, 1e-4
+    nu = (tau - 0.5) / 3.0
+    c = O.lattice(19)[0]
+    with lbm.lbm_batch_create_forced([mask], [tau], [g]) as s:
+        k, _ = lbm.lbm_permeability(s)
+        assert k[0] == 0.0
+        lbm.lbm_step(s, 30)
+        f = lbm.lbm_get_populations(s, 0)
+        lbm.lbm_set_populations(s, 0, f)
+        k, _ = lbm.lbm_permeability(s)
+        jx = float((f * c[:, 0]).sum())
+        assert k[0] == pytest.approx(nu * jx / (mask.size * g), rel=1e-6)
+        lbm.lbm_step(s, 1)
+        lbm.lbm_step_observe(s, 0)
+        k, _ = lbm.lbm_permeability(s)
+        f = lbm.lbm_get_populations(s, 0)
+        assert k[0] == pytest.approx(O.permeability_forced(mask, f, tau, g), rel=1e-5)
+
+
+def test_batch_entry_points_match_the_handle_calls():
+    """lbm_batch_run_to_steady / lbm_batch_permeability / lbm_batch_destroy
+    are the batch forms of the handle calls: same statuses, bit-identical k."""
+    masks = [O.qsgs((20, 40), 1, 0.02, 0.7)[0], O.qsgs((16, 48), 2, 0.02, 0.72)[0]]
+    taus, drhos = [0.8, 1.0], [1e-3, 1e-3]
+    s1 = lbm.lbm_batch_create(masks, taus, drhos)
+    rc1, st1 = lbm.lbm_batch_run_to_steady(s1, 1e-8, 200000)
+    k1 = lbm.lbm_batch_permeability(s1)
+    lbm.lbm_batch_destroy(s1)
+    assert s1.handle is None
+    with lbm.lbm_batch_create(masks, taus, drhos) as s2:
+        rc2, st2, _, _ = lbm.lbm_run_to_steady(s2, 1e-8, 200000)
+        k2, _ = lbm.lbm_permeability(s2)
+    assert rc1 == rc2 and np.array_equal(st1, st2)
+    assert np.array_equal(k1, k2)
+
+
 def test_solve_sharded_without_a_process_group_runs_the_whole_list():
     from paper_1609_09685_gb300 import sharding
     masks = [O.qsgs((20, 40), 1, 0.02, 0.7)[0], O.qsgs((16, 48), 2, 0.02, 0.72)[0]]

@@ -40,15 +40,17 @@ def test_d3q19_workload():
 
 
 def test_time_to_k_takes_the_last_entry_into_the_band():
-    import bench
+    from paper_1609_09685_gb300.warmstart import time_to_k
     t = np.arange(6, dtype=float)
     k = np.array([2.0, 1.5, 1.00005, 0.99, 1.00002, 1.0])
     # the last value outside 1e-4 of the final k is index 3, so the answer is t[4]
-    assert bench.time_to_k(t, k, 1e-4) == 4.0
-    assert bench.time_to_k(t, np.ones(6), 1e-4) == 0.0
-    from paper_1609_09685_gb300 import warmstart
-    assert warmstart.time_to_k(t, k, 1e-4) == (4.0, 4)
-    assert warmstart.time_to_k(t, np.array([]), 1e-4) == (None, None)
+    assert time_to_k(t, k, 1e-4) == (4.0, 4)
+    assert time_to_k(t, np.ones(6), 1e-4) == (0.0, 0)
+    assert time_to_k(t, np.array([]), 1e-4) == (None, None)
+    # against a reference k (the oracle's): the band moves with it
+    assert time_to_k(t, k, 1e-4, k_ref=1.00003) == (4.0, 4)
+    assert time_to_k(t, k, 2e-5, k_ref=1.00003) == (None, None)  # the last k is 3e-5 off
+    assert time_to_k(t, k, 1e-4, k_ref=0.99) == (None, None)
 
 
 def test_warm_start_domain_draws_are_seeded_and_in_range():

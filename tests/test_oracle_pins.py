@@ -317,6 +317,68 @@ def test_plates_3d_match_exact_discrete_solution():
 # Steady state: linearity (Sec. 2, 3D discussion) and flux invariance
 # --------------------------------------------------------------------------
 
+def test_percolates_false_on_blocked_masks():
+    """A full solid column (2D) or plane (3D) across the flow cuts every path,
+    as does an all-solid interior; an open channel percolates."""
+    m = np.zeros((6, 9), np.uint8)
+    assert O.percolates(m)
+    m[:, 4] = 1
+    assert not O.percolates(m)
+    m3 = np.zeros((3, 4, 7), np.uint8)
+    assert O.percolates(m3)
+    m3[:, :, 3] = 1
+    assert not O.percolates(m3)
+    m = np.ones((5, 8), np.uint8)
+    m[:, 0] = 0  # fluid only in the inlet column
+    assert not O.percolates(m)
+    m[:, -1] = 0  # and in the outlet column, with solid between
+    assert not O.percolates(m)
+
+
+def test_percolates_follows_the_lattice_links():
+    """Connectivity is along lattice links: a 2D path of diagonal steps only
+    connects (D2Q9 has the diagonals); in 3D an edge contact connects (D3Q19
+    has the 12 edge directions) but a corner-only contact does not."""
+    m = np.array([[0, 1, 0, 1],
+                  [1, 0, 1, 0]], np.uint8)
+    assert O.percolates(m)
+    m3 = np.ones((2, 2, 2), np.uint8)
+    m3[0, 0, 0] = 0
+    m3[1, 1, 1] = 0  # (x, y, z) -> (x+1, y+1, z+1): corner only
+    assert not O.percolates(m3)
+    m3 = np.ones((2, 2, 2), np.uint8)
+    m3[0, 0, 0] = 0
+    m3[0, 1, 1] = 0  # (x, y) -> (x+1, y+1) in one z plane: an edge link
+    assert O.percolates(m3)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_percolates_matches_connected_component_labelling(dim):
+    """Brute force against scipy's connected-component labelling with the
+    lattice's neighbourhood (8 in 2D; 18 in 3D: faces and edges, no corners)
+    on random masks near the percolation threshold."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(40 + dim)
+    if dim == 2:
+        structure = np.ones((3, 3), bool)
+        shape, ps = (7, 11), (0.4, 0.5, 0.6)
+    else:
+        structure = np.ones((3, 3, 3), bool)
+        for c in ((0, 0, 0), (0, 0, 2), (0, 2, 0), (0, 2, 2), (2, 0, 0), (2, 0, 2), (2, 2, 0), (2, 2, 2)):
+            structure[c] = False
+        shape, ps = (4, 5, 8), (0.5, 0.6, 0.7)
+    seen = set()
+    for p in ps:
+        for _ in range(30):
+            m = (rng.random(shape) < p).astype(np.uint8)
+            lab, _ = ndimage.label(m == 0, structure=structure)
+            a, b = set(lab[..., 0].ravel()) - {0}, set(lab[..., -1].ravel()) - {0}
+            want = bool(a & b)
+            seen.add(want)
+            assert O.percolates(m) == want
+    assert seen == {True, False}
+
+
 def _porous(shape, seed):
     m, _ = O.qsgs(shape, seed, 0.05, 0.75)
     assert O.percolates(m)
