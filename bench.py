@@ -58,6 +58,8 @@ def parse():
                    help="also run the paper's force-driven periodic 3D experiment (100^3, phi 0.748587)")
     p.add_argument("--local-kn", action="store_true",
                    help="also time the local pore-size / local-Kn pass over every domain")
+    p.add_argument("--tile-rows", type=int, default=0,
+                   help="gather step: rows per staged tile (1..4), -1 = direct loads, 0 = library default")
     p.add_argument("--collision", choices=["bgk", "trt"], default="bgk",
                    help="BGK (the paper's model) or TRT with Lambda = 3/16")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -539,13 +541,13 @@ def kernel_table(kt, steps, bytes_per_launch, peak, workload, q):
     return kernels
 
 
-def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak, peak_src):
+def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak, peak_src, tile_rows=0):
     """Per-kernel rooflines of a second workload, timed like the headline one
     (used for the D3Q19 256x128x128 configuration)."""
     wl = get_workload(wl_name, 0)
     q = lattice_q(wl)
     masks = masks_of(lbm, wl, sp)
-    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll)
+    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, tile_rows=tile_rows)
     s = lbm.lbm_batch_create(masks, [d.tau for d in wl.domains], [d.drho for d in wl.domains], opts)
     fluid = s.fluid_nodes
     bpl = 2 * 4 * q * fluid
@@ -591,7 +593,7 @@ def run_native(args):
     taus = [d.tau for d in wl.domains]
     drhos = [d.drho for d in wl.domains]
     coll = lbm.LBM_COLL_TRT if args.collision == "trt" else lbm.LBM_COLL_BGK
-    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll)
+    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, tile_rows=args.tile_rows)
     s = lbm.lbm_batch_create(masks, taus, drhos, opts)
     fluid = s.fluid_nodes
     bytes_per_launch = 2 * 4 * q * fluid
@@ -652,7 +654,7 @@ def run_native(args):
     roof3 = None
     if rank == 0 and not args.no_d3q19 and q == 9:
         roof3 = roofline_of(lbm, "d3q19", sp, stream, N, args.steps, args.warmup, coll, torch.cuda.synchronize,
-                            peak, peak_src)
+                            peak, peak_src, args.tile_rows)
     ttp = measure_ttp(args, lbm, sp) if (not args.no_ttp and rank == 0) else None
     f3d = measure_forced3d(lbm, sp) if (args.forced3d and rank == 0) else None
     kns = measure_kn_sweep(lbm, sp) if (args.kn_sweep and rank == 0) else None
@@ -675,6 +677,7 @@ def run_native(args):
             "config": {
                 "workload": wl.name, "domains": len(wl.domains), "lattice": f"D2Q9" if q == 9 else "D3Q19",
                 "collision": "TRT (Lambda = 3/16)" if args.collision == "trt" else "BGK",
+                "gather_tile_rows": args.tile_rows,
                 "nodes": total_nodes, "fluid_nodes": fluid, "check_interval": N,
                 "step": f"{N - 1} fused stream-collide steps + 1 observing step + FP64 reduction + "
                         "host readback (one convergence-check interval)",

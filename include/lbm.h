@@ -90,6 +90,10 @@ typedef struct lbm_options {
                                 slots); same arithmetic as two pull steps.  0: one pull step at a time. */
     int32_t collision;       /* LBM_COLL_BGK (default) or LBM_COLL_TRT */
     double trt_lambda;       /* TRT: Lambda = (tau - 1/2)(tau_minus - 1/2), > 0 (default 3/16) */
+    int32_t tile_rows;       /* gather step of the in-place pair (D2Q9): 1..4 = staged through shared memory in
+                                tiles of this many rows x 128 nodes (bulk copies by a producer warp, consumed by
+                                four compute warps); 0 or -1 = direct loads per strip (the default, faster on
+                                GB300; D3Q19 always direct).  Every choice gives bit-identical results. */
 } lbm_options;
 
 /* One domain of a batch. */

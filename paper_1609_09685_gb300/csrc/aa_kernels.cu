@@ -3,6 +3,7 @@
 // inlet/outlet bits the local step reads.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <utility>
 
@@ -51,18 +52,17 @@ __device__ __forceinline__ void relax(float (&f)[L::Q], bool edge, bool xin, boo
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = xout ? g[i] : f[i];
     }
-    const float omc = 1.0f - om;
+    const float omc = __fsub_rn(1.0f, om);
     const bool trt = (omm != om);
-    const float hw = 0.5f * om, hwm = 0.5f * omm;
-    const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
-    const float ow3[3] = {3.0f * (omm * (float)L::wd(0)), 3.0f * (omm * (float)L::wd(1)),
-                          3.0f * (omm * (float)L::wd(L::Q - 1))};
-    float dr, jx, jy, jz;
+    const float hw = __fmul_rn(0.5f, om), hwm = __fmul_rn(0.5f, omm);
+    const float ow[3] = {__fmul_rn(om, (float)L::wd(0)), __fmul_rn(om, (float)L::wd(1)),
+                         __fmul_rn(om, (float)L::wd(L::Q - 1))};
+    const float ow3[3] = {__fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(0))),
+                          __fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(1))),
+                          __fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(L::Q - 1)))};
+    float dr, jx, jy, jz, irho, a0, k45;
     moments<L>(f, dr, jx, jy, jz);
-    const float irho = __fdividef(1.0f, rho0 + dr);
-    const float jj = (L::D == 3) ? jx * jx + jy * jy + jz * jz : jx * jx + jy * jy;
-    const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jj, dr) : dr;
-    const float k45 = 4.5f * irho;
+    eq_terms<L, EQ>(dr, jx, jy, jz, rho0, irho, a0, k45);
     const float f0 = f[0];
     float dsum = 0.f;  // sum over i != 0 of f_i - f*_i
 #pragma unroll
@@ -70,14 +70,13 @@ __device__ __forceinline__ void relax(float (&f)[L::Q], bool edge, bool xin, boo
         if (opp<L>(i) < i) continue;
         const int o = opp<L>(i);
         const int cls = (L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
-        const float cj = cdot<L>(i, jx, jy, jz);
-        const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
-        const float anti = ow3[cls] * cj;
+        float sym, anti;
+        pair_terms<L, EQ>(i, jx, jy, jz, a0, k45, ow[cls], ow3[cls], sym, anti);
         const float fi = f[i], fo = f[o];
         pair_relax(fi, fo, sym, anti, omc, hw, hwm, trt, f[i], f[o]);
-        dsum += (fi - f[i]) + (fo - f[o]);
+        dsum = pair_dsum(dsum, fi, fo, f[i], f[o]);
     }
-    f[0] = f0 + dsum;  // mass balance: see the pull kernel
+    f[0] = __fadd_rn(f0, dsum);  // mass balance: see the pull kernel
 }
 
 template <class L, int... Is>
@@ -323,6 +322,366 @@ __global__ void __maxnreg__(LBM_AA_GATHER_REGS_3D) k_aa_gather3(const __grid_con
     else aa_gather_body<L, EQ>(A);
 }
 
+// ---------------------------------------------------------------------------
+// Staged gather step.  The gather step above is latency-bound: its loads
+// depend on the neighbour windows, and the registers that hold loads in
+// flight limit how many rows a warp can batch.  Here the loads go through the
+// bulk-copy engine instead.  A block walks a list of tiles (GatherTile: up to
+// TR rows x kTileSegs segment columns of one domain) with a ring of S
+// shared-memory stages:
+//   - one producer warp copies, for each tile, the tile record, the domain
+//     record, the window records of its source rows and the compact range of
+//     every source row in every plane the tile pulls from (cp.async.bulk,
+//     completion counted in bytes on the stage's `full` mbarrier); it refills
+//     a stage once every consumer has released it (`empty` mbarrier);
+//   - kTileSegs consumer warps, one per segment column, relax the tile's nodes
+//     from shared memory and write each result straight back to the global
+//     slot it came from (the in-place rule of the pair), then release the
+//     stage.
+// A slot a tile uses is read and written only by its own node, so copying
+// whole ranges is safe: slots of other tiles that come along are never used.
+//
+// Slot layout of a stage (2D): the row above the tile (q = 0) holds the planes
+// of the c_y = +1 directions, the row below (q = nrows + 1) those of c_y = -1,
+// each in slot I - Imin of its class; every tile row holds all Q planes.  A row
+// above or below the domain is the specular image of the face row: its slots
+// hold the face row's ranges of the y-flipped planes, so the compute needs no
+// face logic to find a source, only the window of the clamped row.
+// ---------------------------------------------------------------------------
+namespace staged {
+
+constexpr int TW = kTileSegs;
+constexpr int RANGE = TW * 32 + 8;  // floats per (row, plane) slot
+constexpr uint32_t RB = RANGE * 4;  // bytes per slot
+constexpr int HDR = (int)(sizeof(DomainDev) + sizeof(GatherTile));  // domain and tile records
+
+template <class L>
+struct Cls;
+template <>
+struct Cls<D2Q9> {
+    // directions of the row above (c_y = +1) and below (c_y = -1)
+    static constexpr int up0 = find_dir<D2Q9>(0, 1, 0), up1 = find_dir<D2Q9>(1, 1, 0), up2 = find_dir<D2Q9>(-1, 1, 0);
+    static constexpr int dn0 = find_dir<D2Q9>(0, -1, 0), dn1 = find_dir<D2Q9>(1, -1, 0),
+                         dn2 = find_dir<D2Q9>(-1, -1, 0);
+    static constexpr int up_min = 2, dn_min = 4, span = 5;
+};
+static_assert(Cls<D2Q9>::up0 == 2 && Cls<D2Q9>::up1 == 5 && Cls<D2Q9>::up2 == 6, "D2Q9 order");
+static_assert(Cls<D2Q9>::dn0 == 4 && Cls<D2Q9>::dn1 == 8 && Cls<D2Q9>::dn2 == 7, "D2Q9 order");
+
+template <int TR, int S>
+struct Geo2 {
+    static constexpr int NQ = TR + 2;
+    static constexpr int SLOTS = 9 * TR + 2 * Cls<D2Q9>::span;
+    static constexpr int WIN = HDR;                         // window records: NQ x TW uint4
+    static constexpr int RNG = HDR + NQ * TW * 16;          // slots
+    static constexpr int STAGE = RNG + SLOTS * (int)RB;     // bytes per stage
+    static constexpr int BARS = S * STAGE;                  // S full, then S empty mbarriers
+    static constexpr int SMEM = BARS + 16 * S;
+    // first slot of source row q (slot I - Imin for the halo rows)
+    __host__ __device__ static constexpr int slot0(int q, int nrows) {
+        return q == 0 ? -Cls<D2Q9>::up_min
+                      : (q <= nrows ? Cls<D2Q9>::span + 9 * (q - 1) : Cls<D2Q9>::span + 9 * TR - Cls<D2Q9>::dn_min);
+    }
+};
+static_assert(HDR % 16 == 0 && Geo2<4, 2>::STAGE % 16 == 0 && RB % 16 == 0, "16-byte aligned stages and slots");
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: false if the phase has not completed after kWaitTries polls
+// (each poll may suspend the thread for a short, hardware-defined time).
+constexpr int kWaitTries = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of
+// 16), completing `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// What the producer needs of a tile, loaded one tile ahead.
+struct TileRegs {
+    uint32_t dom, yz, shape, dims, wbase, live;
+    uint32_t a0[kTileRowsMax + 2], n16[kTileRowsMax + 2];
+};
+__device__ __forceinline__ void load_tile(const HotArgs& A, uint32_t t, TileRegs& R) {
+    const GatherTile* T = A.tiles + t;
+    R.dom = __ldg(&T->dom);
+    R.yz = __ldg(&T->yz);
+    R.shape = __ldg(&T->shape);
+    R.dims = __ldg(&T->dims);
+    R.wbase = __ldg(&T->wbase);
+#pragma unroll
+    for (int q = 0; q < kTileRowsMax + 2; ++q) {
+        R.a0[q] = __ldg(&T->a0[q]);
+        R.n16[q] = __ldg(&T->n16[q]);
+    }
+}
+
+// Producer: issue the copies of tile t into a stage (every lane of the
+// producer warp).  Lane 0 arms the stage's mbarrier with the byte count before
+// any copy is issued.  A retired domain's tile brings only the two records.
+template <int TR>
+__device__ __forceinline__ void issue_tile2(const HotArgs& A, uint32_t t, const TileRegs& R, unsigned char* stage,
+                                            uint32_t bar) {
+    using C = Cls<D2Q9>;
+    constexpr int WIN = HDR;
+    constexpr int RNG_ = HDR + (TR + 2) * TW * 16;
+    const int lane = threadIdx.x & 31;
+    const int y0 = (int)(R.yz & 0xffffu);
+    const int nrows = (int)(R.shape & 0xffu), nsegs = (int)((R.shape >> 8) & 0xffu);
+    const int ny = (int)(R.dims & 0xffffu), nseg = (int)(R.dims >> 16);
+    const int nq = nrows + 2;
+    const uint32_t PS = A.pstride;
+    const uint32_t rng = saddr(stage + RNG_);
+    uint32_t total = (uint32_t)HDR;
+    if (R.live) {
+        total += (uint32_t)(nq * nsegs * 16);
+#pragma unroll
+        for (int q = 0; q < kTileRowsMax + 2; ++q)
+            if (q < nq) total += ((q == 0 || q == nq - 1) ? 3u : 9u) * 16u * R.n16[q];
+    }
+    if (lane == 0) mbar_arrive_expect(bar, total);
+    __syncwarp();
+    if (lane == 0) bulk_g2s(saddr(stage), A.dom + R.dom, (uint32_t)sizeof(DomainDev), bar);
+    if (lane == 1) bulk_g2s(saddr(stage + sizeof(DomainDev)), A.tiles + t, (uint32_t)sizeof(GatherTile), bar);
+    if (!R.live) return;
+    const float* g = A.dst[0];
+    const int ncopy = nq + 3 + 9 * nrows + 3;
+    for (int c = lane; c < ncopy; c += 32) {
+        if (c < nq) {  // window records of source row q (clamped row)
+            int yc = y0 - 1 + c;
+            yc = yc < 0 ? 0 : (yc >= ny ? ny - 1 : yc);
+            bulk_g2s(saddr(stage + WIN + c * TW * 16), A.win + R.wbase + (uint32_t)yc * (uint32_t)nseg,
+                     (uint32_t)nsegs * 16u, bar);
+            continue;
+        }
+        const int cc = c - nq;
+        int q, plane, slot;
+        if (cc < 3) {  // row above: c_y = +1 planes, y-flipped when it is the image of row 0
+            q = 0;
+            constexpr int f0 = flip<D2Q9>(C::up0, true, false), f1 = flip<D2Q9>(C::up1, true, false),
+                          f2 = flip<D2Q9>(C::up2, true, false);
+            const int I = cc == 0 ? C::up0 : (cc == 1 ? C::up1 : C::up2);
+            const int fI = cc == 0 ? f0 : (cc == 1 ? f1 : f2);
+            slot = Geo2<TR, 1>::slot0(0, nrows) + I;
+            plane = (y0 == 0) ? fI : I;
+        } else if (cc < 3 + 9 * nrows) {
+            q = 1 + (cc - 3) / 9;
+            plane = (cc - 3) % 9;
+            slot = Geo2<TR, 1>::slot0(q, nrows) + plane;
+        } else {  // row below: c_y = -1 planes
+            q = nrows + 1;
+            constexpr int f0 = flip<D2Q9>(C::dn0, true, false), f1 = flip<D2Q9>(C::dn1, true, false),
+                          f2 = flip<D2Q9>(C::dn2, true, false);
+            const int j = cc - 3 - 9 * nrows;
+            const int I = j == 0 ? C::dn0 : (j == 1 ? C::dn1 : C::dn2);
+            const int fI = j == 0 ? f0 : (j == 1 ? f1 : f2);
+            slot = Geo2<TR, 1>::slot0(q, nrows) + I;
+            plane = (y0 + nrows == ny) ? fI : I;
+        }
+        uint32_t n = 0, a0 = 0;
+#pragma unroll
+        for (int k = 0; k < kTileRowsMax + 2; ++k)
+            if (k == q) {
+                n = R.n16[k];
+                a0 = R.a0[k];
+            }
+        if (n == 0) continue;
+        bulk_g2s(rng + (uint32_t)slot * RB, g + (size_t)plane * PS + a0, n * 16u, bar);
+    }
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float ldsf(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldsu(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// Source of direction I: the global element the pull step reads (and the
+// gather step writes back), and the shared-memory address of its staged copy.
+// rb[r]: row bases of the source rows y - 1, y, y + 1.
+template <class L, int I>
+__device__ __forceinline__ void src_staged(const Win (&w)[3], uint32_t PS, uint32_t kd, bool my, const uint32_t (&rb)[3],
+                                           uint32_t& e, uint32_t& sa) {
+    using d = Dir<I, L>;
+    const Win& wn = w[d::row];
+    const bool sf = win_fluid<d::cx>(wn);
+    const uint32_t k = win_idx<d::cx>(wn);
+    const uint32_t plane = (d::cy != 0 && my) ? (uint32_t)d::fy : (uint32_t)I;
+    e = sf ? plane * PS + k : (uint32_t)d::o * PS + kd;
+    sa = sf ? rb[d::row] + (uint32_t)I * RB + 4u * k : rb[1] + (uint32_t)d::o * RB + 4u * kd;
+}
+template <class L, int... Is>
+__device__ __forceinline__ void srcs_staged(const Win (&w)[3], uint32_t PS, uint32_t kd, bool ylo, bool yhi,
+                                            const uint32_t (&rb)[3], uint32_t (&e)[L::Q], uint32_t (&sa)[L::Q],
+                                            std::integer_sequence<int, Is...>) {
+    (src_staged<L, Is>(w, PS, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, rb, e[Is], sa[Is]), ...);
+}
+
+// Consumer warp: relax the nodes of its segment column of the staged tile.
+template <class L, int EQ, int TR>
+__device__ __forceinline__ void compute_tile2(const HotArgs& A, const unsigned char* stage) {
+    constexpr int Q = L::Q;
+    constexpr int WIN = HDR;
+    constexpr int RNG_ = HDR + (TR + 2) * TW * 16;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const DomainDev& D = *reinterpret_cast<const DomainDev*>(stage);
+    const GatherTile& T = *reinterpret_cast<const GatherTile*>(stage + sizeof(DomainDev));
+    if (!D.active) return;
+    const uint32_t shape = T.shape;
+    const int nsegs = (int)((shape >> 8) & 0xffu);
+    if (wid >= nsegs) return;
+    const int y0 = (int)(T.yz & 0xffffu);
+    const int nrows = (int)(shape & 0xffu), s0 = (int)(shape >> 16);
+    const int s = s0 + wid;
+    const int x = s * kSegW + lane;
+    const bool xin = (x == 0), xout = (x == D.nx - 1);
+    const bool edge = (s == 0) || (s == D.nseg - 1);
+    const int ny = D.ny;
+    const float drho_in = D.drho_in, rho0 = D.rho0, om = D.omega, omm = D.omega_m;
+    const uint32_t lmask = (1u << lane) - 1u;
+    const uint32_t PS = A.pstride;
+    float* const g = A.dst[0];
+    const uint32_t wb = saddr(stage + WIN) + (uint32_t)wid * 16u;
+    const uint32_t rng = saddr(stage + RNG_);
+    auto rowbase = [&](int q) {
+        return rng + (uint32_t)(Geo2<TR, 1>::slot0(q, nrows) * (int)RB) - 4u * T.a0[q];
+    };
+    // windows and row bases of the source rows y - 1, y, y + 1, slid down the column
+    Win w[3];
+    uint32_t rb[3];
+    w[0] = make_win(lds128(wb), lane, lmask);
+    w[1] = make_win(lds128(wb + TW * 16), lane, lmask);
+    rb[0] = rowbase(0);
+    rb[1] = rowbase(1);
+#pragma unroll 1
+    for (int r = 0; r < nrows; ++r) {
+        const int y = y0 + r;
+        w[2] = make_win(lds128(wb + (uint32_t)((r + 2) * TW * 16)), lane, lmask);
+        rb[2] = rowbase(r + 2);
+        const bool fl = win_fluid<0>(w[1]);
+        const uint32_t kd = win_idx<0>(w[1]);
+        uint32_t e[Q], sa[Q];
+        srcs_staged<L>(w, PS, kd, y == 0, y == ny - 1, rb, e, sa, std::make_integer_sequence<int, Q>{});
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = ldsf(sa[i]);
+        relax<L, EQ>(f, edge, xin, xout, drho_in, rho0, om, omm);
+        if (fl) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[e[opp<L>(i)]] = f[i];
+        }
+        w[0] = w[1];
+        w[1] = w[2];
+        rb[0] = rb[1];
+        rb[1] = rb[2];
+    }
+}
+
+}  // namespace staged
+
+// Producer warp (the last one) and kTileSegs consumer warps; see above.
+template <class L, int EQ, int TR, int S>
+__global__ void __launch_bounds__((kTileSegs + 1) * 32) k_aa_gather_staged(const __grid_constant__ HotArgs A) {
+    using G = staged::Geo2<TR, S>;
+    extern __shared__ __align__(128) unsigned char sm_stage[];
+    __shared__ int failed;
+    const uint32_t full0 = staged::saddr(sm_stage + G::BARS), empty0 = full0 + 8u * S;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < S; ++s) {
+            staged::mbar_init(full0 + 8u * s, 1);
+            staged::mbar_init(empty0 + 8u * s, kTileSegs);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t issued = 0, consumed = 0;
+    if (wid == kTileSegs) {
+        // producer: one tile ahead in registers, up to S tiles ahead in shared memory
+        uint32_t t = blockIdx.x;
+        staged::TileRegs cur, nxt;
+        if (t < A.ntiles) {
+            staged::load_tile(A, t, cur);
+            cur.live = __ldg(&A.dom[cur.dom].active) != 0;
+        }
+#pragma unroll 1
+        for (uint32_t j = 0; t < A.ntiles; ++j, t += gridDim.x) {
+            const uint32_t tn = t + gridDim.x;
+            if (tn < A.ntiles) staged::load_tile(A, tn, nxt);
+            const int s = (int)(j % S);
+            if (j >= S && !staged::mbar_wait(empty0 + 8u * s, ((j / S) - 1) & 1u)) {
+                if (lane == 0) atomicOr(&failed, 1);
+                break;
+            }
+            staged::issue_tile2<TR>(A, t, cur, sm_stage + s * G::STAGE, full0 + 8u * s);
+            ++issued;
+            if (tn < A.ntiles) {
+                nxt.live = __ldg(&A.dom[nxt.dom].active) != 0;
+                cur = nxt;
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (uint32_t j = 0, t = blockIdx.x; t < A.ntiles; ++j, t += gridDim.x) {
+            const int s = (int)(j % S);
+            if (!staged::mbar_wait(full0 + 8u * s, (j / S) & 1u)) {
+                if (lane == 0) atomicOr(&failed, 1);
+                break;
+            }
+            staged::compute_tile2<L, EQ, TR>(A, sm_stage + s * G::STAGE);
+            ++consumed;
+            __syncwarp();
+            if (lane == 0) staged::mbar_arrive(empty0 + 8u * s);
+        }
+    }
+    __syncthreads();
+    if (failed) {
+        // a copy never completed: report it and give the copies the producer
+        // issued one more bounded wait before the block exits
+        if (threadIdx.x == 0) atomicOr(A.err, 1u);
+        if (wid == kTileSegs && lane == 0)
+            for (uint32_t j = 0; j < issued; ++j) staged::mbar_wait(full0 + 8u * (j % S), (j / S) & 1u);
+    }
+    (void)consumed;
+}
+
 // Local step of the pair: own slots only, pre-collision f_j from slot opp(j),
 // post-collision f*_j to slot j.  It needs no geometry, so it runs over the
 // compact index directly: each lane takes V consecutive slots as one aligned
@@ -422,8 +781,57 @@ inline unsigned aa_blocks(uint32_t nitems, int threads) {
 }
 }  // namespace
 
+// Stages of the staged gather step's ring, per tile height.
+#ifndef LBM_STAGED_STAGES
+#define LBM_STAGED_STAGES 3
+#endif
+// Staged gather step: one persistent block per resident slot (occupancy x SMs,
+// found once per device), each walking the tile list with stride gridDim.x.
+template <class L, int EQ, int TR>
+static cudaError_t staged_launch(const HotArgs& A, cudaStream_t st) {
+    static_assert(L::Q == 9, "the staged gather step is written for D2Q9");
+    constexpr int S = TR <= 2 ? LBM_STAGED_STAGES + 1 : LBM_STAGED_STAGES;
+    using G = staged::Geo2<TR, S>;
+    if (A.ntiles == 0) return cudaSuccess;
+    auto kern = k_aa_gather_staged<L, EQ, TR, S>;
+    static std::atomic<int> grid_of[64];  // resident blocks on device d (0 = not yet known)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    int grid = grid_of[dev].load();
+    if (grid == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (kTileSegs + 1) * 32, G::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid = std::max(per_sm, 1) * std::max(sms, 1);
+        grid_of[dev].store(grid);
+    }
+    const unsigned nb = (unsigned)std::min<uint32_t>(A.ntiles, (uint32_t)grid);
+    kern<<<nb, (kTileSegs + 1) * 32, G::SMEM, st>>>(A);
+    return cudaGetLastError();
+}
+
 template <class L, int EQ>
-static cudaError_t aa_half_launch(int half, int threads, const HotArgs& A, cudaStream_t st) {
+static cudaError_t staged_dispatch(int rows, const HotArgs& A, cudaStream_t st) {
+    if constexpr (L::Q == 9) {
+        switch (rows) {
+            case 1: return staged_launch<L, EQ, 1>(A, st);
+            case 2: return staged_launch<L, EQ, 2>(A, st);
+            case 3: return staged_launch<L, EQ, 3>(A, st);
+            case 4: return staged_launch<L, EQ, 4>(A, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class L, int EQ>
+static cudaError_t aa_half_launch(int half, int threads, int tile_rows, const HotArgs& A, cudaStream_t st) {
+    if (half == 0 && tile_rows > 0) return staged_dispatch<L, EQ>(tile_rows, A, st);
     if (half == 0) {
         const unsigned nb = aa_blocks(A.nitems, threads);
         if (nb == 0) return cudaSuccess;
@@ -453,22 +861,27 @@ static cudaError_t aa_half_launch(int half, int threads, const HotArgs& A, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, int threads, cudaStream_t st) {
+cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, int threads, int tile_rows,
+                           cudaStream_t st) {
     if (threads <= 0) threads = 128;
     for (int i = 0; i < 19; ++i) {
         A.dst[i] = i < q ? g + (size_t)i * A.pstride : nullptr;
         A.src[i] = A.dst[i];
     }
     if (q == 9)
-        return eq == 0 ? aa_half_launch<D2Q9, 0>(half, threads, A, st) : aa_half_launch<D2Q9, 1>(half, threads, A, st);
-    return eq == 0 ? aa_half_launch<D3Q19, 0>(half, threads, A, st) : aa_half_launch<D3Q19, 1>(half, threads, A, st);
+        return eq == 0 ? aa_half_launch<D2Q9, 0>(half, threads, tile_rows, A, st)
+                       : aa_half_launch<D2Q9, 1>(half, threads, tile_rows, A, st);
+    return eq == 0 ? aa_half_launch<D3Q19, 0>(half, threads, tile_rows, A, st)
+                   : aa_half_launch<D3Q19, 1>(half, threads, tile_rows, A, st);
 }
 
-cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, cudaStream_t st) {
-    cudaError_t e = launch_aa_half(q, eq, 0, A, g, threads, st);
+cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, int tile_rows, cudaStream_t st) {
+    cudaError_t e = launch_aa_half(q, eq, 0, A, g, threads, tile_rows, st);
     if (e != cudaSuccess) return e;
-    return launch_aa_half(q, eq, 1, A, g, threads, st);
+    return launch_aa_half(q, eq, 1, A, g, threads, tile_rows, st);
 }
+
+int staged_gather_lattice(int q) { return q == 9; }
 
 int local_step_vector(int q) { return q == 9 ? LocalVec<D2Q9>::value : LocalVec<D3Q19>::value; }
 

@@ -89,6 +89,9 @@ struct lbm_solver {
     uint2* d_vitems = nullptr;  // local-step work items
     uint32_t nvitems = 0;
     uint32_t* d_face = nullptr;  // inlet/outlet bits per compact slot
+    GatherTile* d_tiles = nullptr;  // staged gather step: tile list
+    uint32_t ntiles = 0;
+    int tile_rows = 0;              // rows per tile of the staged gather step (0: direct gather step)
     bool forced = false;         // force-driven, every face periodic (lbm_batch_create_forced)
     bool obs_only = false;       // the last observation was taken without stepping
     float* d_gforce = nullptr;   // body acceleration per domain (force-driven solvers)
@@ -126,7 +129,15 @@ struct lbm_solver {
         A.vitems = d_vitems;
         A.nvitems = nvitems;
         A.face = d_face;
+        A.tiles = d_tiles;
+        A.ntiles = ntiles;
+        A.err = err_word();
         return A;
+    }
+    // device error word, kept right after the observables so that every
+    // observation brings it back to the host
+    uint32_t* err_word() const {
+        return d_obs ? reinterpret_cast<uint32_t*>(d_obs + (size_t)kNumObs * dom.size()) : nullptr;
     }
 };
 
@@ -216,6 +227,7 @@ void free_solver(lbm_handle h) {
         dfree(h, h->d_items);
         dfree(h, h->d_vitems);
         dfree(h, h->d_face);
+        dfree(h, h->d_tiles);
         dfree(h, h->d_mask);
         dfree(h, h->d_g[0]);
         dfree(h, h->d_g[1]);
@@ -303,12 +315,13 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     } else if (h->opt.in_place_pairs) {
         for (; plain >= 2; plain -= 2) {
             if (!prof) {
-                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->tile_rows, h->st));
                 continue;
             }
             for (int half = 0; half < 2; ++half) {
                 CK(h, prof->mark(h->st));
-                CK(h, launch_aa_half(h->q, h->eq, half, A, h->d_g[h->cur], h->opt.block_threads, h->st));
+                CK(h, launch_aa_half(h->q, h->eq, half, A, h->d_g[h->cur], h->opt.block_threads, h->tile_rows,
+                                     h->st));
                 CK(h, prof->mark(h->st));
                 prof->kind.push_back(half);
             }
@@ -329,7 +342,7 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
         h->obs_only = (n == 0);
         if (n == 0) CK(h, launch_observe(h->q, G, h->d_g[h->cur], h->d_uprev, h->d_partials, h->st));
         CK(h, launch_reduce_obs(h->d_dom, (int)h->dom.size(), h->d_partials, h->d_obs, n > 0, h->st));
-        CK(h, cudaMemcpyAsync(h->h_obs, h->d_obs, sizeof(double) * kNumObs * h->dom.size(),
+        CK(h, cudaMemcpyAsync(h->h_obs, h->d_obs, sizeof(double) * (kNumObs * h->dom.size() + 1),
                               cudaMemcpyDeviceToHost, h->st));
     }
     return LBM_OK;
@@ -373,7 +386,18 @@ lbm_status run_steps(lbm_handle h, int64_t n, bool obs) {
     return LBM_OK;
 }
 
-void store_obs(lbm_handle h) {
+lbm_status device_error(lbm_handle h, uint32_t word) {
+    if (word == 0) return LBM_OK;
+    char buf[160];
+    std::snprintf(buf, sizeof(buf),
+                  "device error word 0x%x: a staged gather copy did not complete within its wait limit", word);
+    return fail(h, LBM_ERR_INTERNAL, buf);
+}
+
+lbm_status store_obs(lbm_handle h) {
+    uint32_t word = 0;
+    std::memcpy(&word, h->h_obs + (size_t)kNumObs * h->dom.size(), sizeof(word));
+    if (word) return device_error(h, word);
     for (size_t d = 0; d < h->dom.size(); ++d) {
         if (!h->dom[d].active) continue;
         std::memcpy(h->dom[d].obs, h->h_obs + d * kNumObs, sizeof(double) * kNumObs);
@@ -390,6 +414,7 @@ void store_obs(lbm_handle h) {
                                                                    : 0.0);
         h->dom[d].has_obs = true;
     }
+    return LBM_OK;
 }
 
 // Copy a retired domain's populations into the other buffer so both hold its
@@ -592,7 +617,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255 ||
         (o.in_place_pairs != 0 && o.in_place_pairs != 1) ||
         (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
-        !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)))
+        !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax)
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (gforce) {
         o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
@@ -770,6 +795,59 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.nitems = (uint32_t)items.size() - G.item_base;
     }
     h->nitems = (uint32_t)items.size();
+    // Tiles of the staged gather step (D2Q9 in-place pairs): per domain and z
+    // plane, TR rows x kTileSegs segment columns, column groups innermost;
+    // all-solid tiles are left out.  For each source row (the rows above and
+    // below included, clamped onto the domain) the 16-byte aligned compact
+    // range that covers nodes 32 s0 - 1 .. 32 (s0 + nsegs).
+    {
+        int tr = 0;
+        if (q == 9 && o.in_place_pairs && !gforce && o.tile_rows > 0) tr = o.tile_rows;
+        for (int d = 0; d < n && tr; ++d)
+            if (h->hdom[d].nseg > 65535) tr = 0;  // s0 is packed in 16 bits
+        std::vector<GatherTile> tiles;
+        for (int d = 0; d < n && tr; ++d) {
+            const DomainDev& G = h->hdom[d];
+            for (int z = 0; z < G.nz; ++z)
+                for (int y0 = 0; y0 < G.ny; y0 += tr)
+                    for (int s0 = 0; s0 < G.nseg; s0 += kTileSegs) {
+                        const int nr = std::min(tr, G.ny - y0), ns = std::min(kTileSegs, G.nseg - s0);
+                        auto seg = [&](int y, int sx) {
+                            return G.seg_base + ((uint32_t)z * G.ny + (uint32_t)y) * (uint32_t)G.nseg + (uint32_t)sx;
+                        };
+                        bool any = false;
+                        for (int r = 0; r < nr && !any; ++r)
+                            for (int k = 0; k < ns && !any; ++k) any = smask[seg(y0 + r, s0 + k)] != 0u;
+                        if (!any) continue;
+                        GatherTile T{};
+                        T.dom = (uint32_t)d;
+                        T.yz = (uint32_t)y0 | ((uint32_t)z << 16);
+                        T.shape = (uint32_t)nr | ((uint32_t)ns << 8) | ((uint32_t)s0 << 16);
+                        T.dims = (uint32_t)G.ny | ((uint32_t)G.nseg << 16);
+                        T.wbase = seg(0, s0);
+                        for (int qq = 0; qq < nr + 2; ++qq) {
+                            const int yc = std::min(std::max(y0 - 1 + qq, 0), G.ny - 1);
+                            const uint32_t g0 = seg(yc, s0), g1 = seg(yc, s0 + ns - 1);
+                            const uint32_t left = s0 > 0 ? (smask[g0 - 1] >> 31) & 1u : 0u;
+                            const uint32_t right = s0 + ns < G.nseg ? smask[g1 + 1] & 1u : 0u;
+                            const uint32_t lo = off[g0] - left;
+                            const uint32_t hi = off[g1] + (uint32_t)__builtin_popcount(smask[g1]) + right;
+                            const uint32_t a0 = lo & ~3u, a1 = (hi + 3u) & ~3u;
+                            T.a0[qq] = a0;
+                            T.n16[qq] = (uint16_t)(hi > lo ? (a1 - a0) / 4u : 0u);
+                        }
+                        tiles.push_back(T);
+                    }
+        }
+        h->tile_rows = tr;
+        h->ntiles = (uint32_t)tiles.size();
+        if (tr) {
+            CKC(dmalloc(h, &h->d_tiles, sizeof(GatherTile) * std::max<size_t>(tiles.size(), 1)));
+            CKC(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(GatherTile) * tiles.size(), cudaMemcpyHostToDevice,
+                                h->st));
+            CKC(cudaStreamSynchronize(h->st));
+        }
+    }
     CKC(dmalloc(h, &h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
     CKC(cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
     CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
@@ -787,7 +865,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(dmalloc(h, &h->d_g[1], sizeof(float) * q * h->pstride));
     CKC(dmalloc(h, &h->d_uprev, sizeof(float) * D * h->pstride));
     CKC(dmalloc(h, &h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
-    CKC(dmalloc(h, &h->d_obs, sizeof(double) * kNumObs * n));
+    CKC(dmalloc(h, &h->d_obs, sizeof(double) * (kNumObs * n + 1)));
+    CKC(cudaMemsetAsync(h->d_obs, 0, sizeof(double) * (kNumObs * n + 1), h->st));
     if (gforce) {
         std::vector<float> gf(n);
         for (int d = 0; d < n; ++d) gf[d] = (float)gforce[d];
@@ -795,7 +874,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         CKC(cudaMemcpyAsync(h->d_gforce, gf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->st));
         CKC(cudaStreamSynchronize(h->st));
     }
-    CKC(cudaMallocHost(&h->h_obs, sizeof(double) * kNumObs * n));
+    CKC(cudaMallocHost(&h->h_obs, sizeof(double) * (kNumObs * n + 1)));
     CKC(cudaMemsetAsync(h->d_g[0], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(cudaMemsetAsync(h->d_g[1], 0, sizeof(float) * q * h->pstride, h->st));
     CKC(launch_init(q, h->geom(), h->d_g[0], h->d_uprev, h->st));
@@ -905,6 +984,12 @@ lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int
     lbm_status s = enqueue_steps(h, nsteps, false, &prof);
     if (s != LBM_OK) return s;
     CK(h, cudaStreamSynchronize(h->st));
+    {
+        uint32_t word = 0;
+        CK(h, cudaMemcpy(&word, h->err_word(), sizeof(word), cudaMemcpyDeviceToHost));
+        s = device_error(h, word);
+        if (s != LBM_OK) return s;
+    }
     for (size_t i = 0; i < prof.kind.size(); ++i) {
         float ms = 0.f;
         CK(h, cudaEventElapsedTime(&ms, prof.ev[2 * i], prof.ev[2 * i + 1]));
@@ -924,7 +1009,8 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {
     if (s != LBM_OK) return s;
     CK(h, cudaStreamSynchronize(h->st));
     h->step += nsteps;
-    store_obs(h);
+    s = store_obs(h);
+    if (s != LBM_OK) return s;
     if (obs) std::memcpy(obs, h->h_obs, sizeof(double) * kNumObs * h->dom.size());
     return LBM_OK;
 }
@@ -967,7 +1053,8 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
         CK(h, cudaStreamSynchronize(h->st));
         taken += k;
         h->step += k;
-        store_obs(h);
+        s = store_obs(h);
+        if (s != LBM_OK) return s;
         bool retired = false;
         for (size_t d = 0; d < n; ++d) {
             DomainHost& D = h->dom[d];
@@ -1060,7 +1147,8 @@ lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
         lbm_status s = enqueue_steps(h, 0, true);
         if (s != LBM_OK) return s;
         CK(h, cudaStreamSynchronize(h->st));
-        store_obs(h);
+        s = store_obs(h);
+        if (s != LBM_OK) return s;
     }
     lbm_status rs = LBM_OK;
     for (size_t d = 0; d < h->dom.size(); ++d) {

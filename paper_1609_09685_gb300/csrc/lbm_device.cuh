@@ -59,8 +59,9 @@ __host__ __device__ constexpr int flip(int i, bool fy, bool fz) {
     return find_dir<L>(L::c(i, 0), fy ? -L::c(i, 1) : L::c(i, 1), fz ? -L::c(i, 2) : L::c(i, 2));
 }
 
-// One domain of a batch as the kernels see it.
-struct DomainDev {
+// One domain of a batch as the kernels see it (16-byte aligned: the staged
+// gather step copies a domain's record with a bulk copy).
+struct alignas(16) DomainDev {
     int32_t nx, ny, nz;  // nz = 1 in 2D
     int32_t nseg;        // segments per x-row, ceil(nx / 32)
     uint32_t seg_base;   // first global segment of the domain
@@ -76,6 +77,7 @@ struct DomainDev {
     uint32_t fluid_begin;  // compact index of the domain's first fluid node (a multiple of 32)
     uint32_t fluid_end;    // one past its last fluid node
 };
+static_assert(sizeof(DomainDev) == 80, "DomainDev is 80 bytes");
 
 // Neighbour window of one segment, read by the stream-collide kernel:
 //   x = lo | hi << 32 holds 34 fluid bits, bit k <-> node x = 32 s - 1 + k
@@ -91,6 +93,28 @@ using SegWindow = uint4;
 //   z = y0 | z << 16;                  w = s.
 using StripItem = uint4;
 
+// Tile of the staged gather step: up to kTileRowsMax rows (y0 .. y0 + nrows - 1)
+// of one z plane at nsegs <= kTileSegs consecutive segment columns s0 .. of one
+// domain, with the compact range of every source row it pulls from.  Source
+// row q (0 .. nrows + 1) of plane zq is row y0 - 1 + q clamped onto the domain
+// (a clamped row stands for the mirror image at a specular face); its range
+// [a0, a0 + 4 n16) covers the compact slots of nodes x = 32 s0 - 1 ..
+// 32 (s0 + nsegs), widened to 16-byte boundaries (n16 = 0: no fluid there).
+// Index of (plane zq, row q): zq * 6 + q, zq = 0 (z - 1), 1 (z), 2 (z + 1); 2D
+// tiles use zq = 0 only.
+constexpr int kTileSegs = 4;
+constexpr int kTileRowsMax = 4;
+struct GatherTile {
+    uint32_t dom;
+    uint32_t yz;     // y0 | z << 16
+    uint32_t shape;  // nrows | nsegs << 8 | s0 << 16
+    uint32_t dims;   // ny | nseg << 16 of the domain
+    uint32_t a0[18];
+    uint16_t n16[18];
+    uint32_t wbase;  // window record of (plane z, row 0, segment s0)
+};
+static_assert(sizeof(GatherTile) == 128, "GatherTile is 128 bytes");
+
 // Arguments of the hot stream-collide kernel.
 struct HotArgs {
     const DomainDev* dom;
@@ -103,6 +127,9 @@ struct HotArgs {
     const uint2* vitems;     // local-step work items: (first compact index, domain), one warp each
     uint32_t nvitems;
     const uint32_t* face;    // 2 bits per compact slot: bit 0 inlet (x = 0), bit 1 outlet (x = N_x - 1)
+    const GatherTile* tiles; // staged gather step: tile list
+    uint32_t ntiles;
+    uint32_t* err;           // device error word (bit 0: a staged copy never completed)
 };
 
 // Arguments shared by every segment kernel.

@@ -98,12 +98,14 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     const bool edge = (it.w == 0) || ((int)it.w == D.nseg - 1);
     // omega-scaled weights by |c|^2 class (0 rest, 1 axis, 2 diagonal), and 3x
     // the omega_m-scaled ones (the odd part's rate; omega_m = omega for BGK)
-    const float om = D.omega, omc = 1.0f - D.omega, omm = D.omega_m;
+    const float om = D.omega, omc = __fsub_rn(1.0f, D.omega), omm = D.omega_m;
     const bool trt = (omm != om);
-    const float hw = 0.5f * om, hwm = 0.5f * omm;
-    const float ow[3] = {om * (float)L::wd(0), om * (float)L::wd(1), om * (float)L::wd(L::Q - 1)};
-    const float ow3[3] = {3.0f * (omm * (float)L::wd(0)), 3.0f * (omm * (float)L::wd(1)),
-                          3.0f * (omm * (float)L::wd(L::Q - 1))};
+    const float hw = __fmul_rn(0.5f, om), hwm = __fmul_rn(0.5f, omm);
+    const float ow[3] = {__fmul_rn(om, (float)L::wd(0)), __fmul_rn(om, (float)L::wd(1)),
+                         __fmul_rn(om, (float)L::wd(L::Q - 1))};
+    const float ow3[3] = {__fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(0))),
+                          __fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(1))),
+                          __fmul_rn(3.0f, __fmul_rn(omm, (float)L::wd(L::Q - 1)))};
     float* const dst0 = A.dst[0];  // plane i starts at dst0 + i * PS
     constexpr int SL = stage_slots<L, OBS>();
     float* wbuf = smem + (size_t)wid * S * SL * 32;
@@ -217,15 +219,12 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
 #pragma unroll
                 for (int i = 0; i < Q; ++i) f[i] = xout ? g[i] : f[i];
             }
-            float dr, jx, jy, jz;
+            float dr, jx, jy, jz, irho, a0, k45;
             moments<L>(f, dr, jx, jy, jz);
-            const float irho = __fdividef(1.0f, D.rho0 + dr);
+            eq_terms<L, EQ>(dr, jx, jy, jz, D.rho0, irho, a0, k45);
             if (fl) {
                 // BGK (or TRT) by opposite pairs: f* = (1 - omega) f + omega w (a0 + 4.5 (c.j)^2/rho +- 3 c.j),
                 // a0 = drho - 1.5 |j|^2 / rho (quadratic) or drho (linear).
-                const float jj = (L::D == 3) ? jx * jx + jy * jy + jz * jz : jx * jx + jy * jy;
-                const float a0 = (EQ == 0) ? fmaf(-1.5f * irho, jj, dr) : dr;
-                const float k45 = 4.5f * irho;
                 float* const dk = dst0 + kk;
                 float dsum = 0.f;  // sum over i != 0 of f_i - f*_i
                 float link = 0.f;  // post-collision populations that cross an interior x plane
@@ -234,14 +233,13 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                     if (opp<L>(i) < i) continue;
                     const int o = opp<L>(i);
                     const int cls = (L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
-                    const float cj = cdot<L>(i, jx, jy, jz);
-                    const float sym = ow[cls] * ((EQ == 0) ? fmaf(k45 * cj, cj, a0) : a0);
-                    const float anti = ow3[cls] * cj;
+                    float sym, anti;
+                    pair_terms<L, EQ>(i, jx, jy, jz, a0, k45, ow[cls], ow3[cls], sym, anti);
                     float out_i, out_o;
                     pair_relax(f[i], f[o], sym, anti, omc, hw, hwm, trt, out_i, out_o);
                     dk[(uint32_t)i * PS] = out_i;
                     dk[(uint32_t)o * PS] = out_o;
-                    dsum += (f[i] - out_i) + (f[o] - out_o);
+                    dsum = pair_dsum(dsum, f[i], f[o], out_i, out_o);
                     if (OBS && L::c(i, 0) != 0) {
                         // direction i reaches fluid iff the source of o is fluid, and vice versa
                         if ((sfq[st] >> o) & 1u) link += (float)L::c(i, 0) * out_i;
@@ -259,7 +257,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
                 // amplify it (a 512 x 256 domain's k drifted 4e-4 from the FP64
                 // value with the rest population from its own formula, 3e-6
                 // with this balance).
-                dk[0] = f[0] + dsum;
+                dk[0] = __fadd_rn(f[0], dsum);
                 if (OBS) {
                     // Within one strip (at most 8 rows x 32 lanes) the sums are
                     // FP32 -- the FP64 rate of this part is low -- and each

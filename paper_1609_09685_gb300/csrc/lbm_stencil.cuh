@@ -60,28 +60,40 @@ __device__ __forceinline__ float warp_maxf(float v) {
 // Written generically; in 2D it reduces to Zou & He (1997), in 3D to the
 // Hecht & Harting (2010) form.  The shifted weights cancel because the c_x = 0
 // weights plus twice the c_x = -side weights sum to one.
+//
+// Every floating-point operation of the collision helpers below is written
+// out (fmaf, or the __f*_rn intrinsics, which the compiler never fuses), so
+// that a node relaxed by any kernel -- pull step, gather step (direct or
+// staged), local step -- gets the same bits from the same populations.
 template <class L, int SIDE>
 __device__ __forceinline__ void zou_he(float (&f)[L::Q], float drho_b) {
     float s0 = 0.f, sin = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         if (L::c(i, 0) == 0) {
-            s0 += f[i];
-            ny += (float)L::c(i, 1) * f[i];
-            nz += (float)L::c(i, 2) * f[i];
+            s0 = __fadd_rn(s0, f[i]);
+            if (L::c(i, 1) > 0) ny = __fadd_rn(ny, f[i]);
+            if (L::c(i, 1) < 0) ny = __fsub_rn(ny, f[i]);
+            if (L::c(i, 2) > 0) nz = __fadd_rn(nz, f[i]);
+            if (L::c(i, 2) < 0) nz = __fsub_rn(nz, f[i]);
         } else if (L::c(i, 0) == -SIDE) {
-            sin += f[i];
+            sin = __fadd_rn(sin, f[i]);
         }
     }
-    const float rux = (float)SIDE * (drho_b - (s0 + 2.f * sin));
-    ny *= 0.5f;
-    nz *= 0.5f;
+    const float r = __fsub_rn(drho_b, __fadd_rn(s0, __fmul_rn(2.f, sin)));
+    const float rux = SIDE > 0 ? r : -r;
+    ny = __fmul_rn(0.5f, ny);
+    nz = __fmul_rn(0.5f, nz);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         if (L::c(i, 0) == SIDE) {
-            const float w6 = (float)(6.0 * L::wd(i));
-            f[i] = f[opp<L>(i)] + (float)SIDE * w6 * rux - (float)L::c(i, 1) * ny -
-                   (float)L::c(i, 2) * nz;
+            const float sw6 = (float)(SIDE * 6.0 * L::wd(i));
+            float t = fmaf(sw6, rux, f[opp<L>(i)]);
+            if (L::c(i, 1) > 0) t = __fsub_rn(t, ny);
+            if (L::c(i, 1) < 0) t = __fadd_rn(t, ny);
+            if (L::c(i, 2) > 0) t = __fsub_rn(t, nz);
+            if (L::c(i, 2) < 0) t = __fadd_rn(t, nz);
+            f[i] = t;
         }
     }
 }
@@ -126,12 +138,12 @@ __device__ __forceinline__ bool win_fluid(const Win& w) {
 template <class L>
 __device__ __forceinline__ float cdot(int i, float vx, float vy, float vz) {
     float r = 0.f;
-    if (L::c(i, 0) > 0) r += vx;
-    if (L::c(i, 0) < 0) r -= vx;
-    if (L::c(i, 1) > 0) r += vy;
-    if (L::c(i, 1) < 0) r -= vy;
-    if (L::c(i, 2) > 0) r += vz;
-    if (L::c(i, 2) < 0) r -= vz;
+    if (L::c(i, 0) > 0) r = __fadd_rn(r, vx);
+    if (L::c(i, 0) < 0) r = __fsub_rn(r, vx);
+    if (L::c(i, 1) > 0) r = __fadd_rn(r, vy);
+    if (L::c(i, 1) < 0) r = __fsub_rn(r, vy);
+    if (L::c(i, 2) > 0) r = __fadd_rn(r, vz);
+    if (L::c(i, 2) < 0) r = __fsub_rn(r, vz);
     return r;
 }
 // first moments: density deviation and the momentum components, from the
@@ -144,14 +156,37 @@ __device__ __forceinline__ void moments(const float (&f)[L::Q], float& dr, float
     jz = 0.f;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        dr += f[i];
-        if (L::c(i, 0) > 0) jx += f[i];
-        if (L::c(i, 0) < 0) jx -= f[i];
-        if (L::c(i, 1) > 0) jy += f[i];
-        if (L::c(i, 1) < 0) jy -= f[i];
-        if (L::c(i, 2) > 0) jz += f[i];
-        if (L::c(i, 2) < 0) jz -= f[i];
+        dr = __fadd_rn(dr, f[i]);
+        if (L::c(i, 0) > 0) jx = __fadd_rn(jx, f[i]);
+        if (L::c(i, 0) < 0) jx = __fsub_rn(jx, f[i]);
+        if (L::c(i, 1) > 0) jy = __fadd_rn(jy, f[i]);
+        if (L::c(i, 1) < 0) jy = __fsub_rn(jy, f[i]);
+        if (L::c(i, 2) > 0) jz = __fadd_rn(jz, f[i]);
+        if (L::c(i, 2) < 0) jz = __fsub_rn(jz, f[i]);
     }
+}
+
+// Node terms of the (shifted) equilibrium: 1/rho, a0 = drho - 1.5 |j|^2 / rho
+// (quadratic) or drho (linear), and 4.5/rho.
+template <class L, int EQ>
+__device__ __forceinline__ void eq_terms(float dr, float jx, float jy, float jz, float rho0, float& irho, float& a0,
+                                         float& k45) {
+    irho = __fdividef(1.0f, __fadd_rn(rho0, dr));
+    const float jj =
+        (L::D == 3) ? fmaf(jx, jx, fmaf(jy, jy, __fmul_rn(jz, jz))) : fmaf(jx, jx, __fmul_rn(jy, jy));
+    a0 = (EQ == 0) ? fmaf(__fmul_rn(-1.5f, irho), jj, dr) : dr;
+    k45 = __fmul_rn(4.5f, irho);
+}
+
+// Even and odd equilibrium terms of the opposite pair (i, opp i):
+// sym = omega w (a0 + 4.5 (c_i . j)^2 / rho), anti = omega_m 3 w (c_i . j);
+// ow, ow3 are omega w and 3 omega_m w of the pair's weight class.
+template <class L, int EQ>
+__device__ __forceinline__ void pair_terms(int i, float jx, float jy, float jz, float a0, float k45, float ow,
+                                           float ow3, float& sym, float& anti) {
+    const float cj = cdot<L>(i, jx, jy, jz);
+    sym = __fmul_rn(ow, (EQ == 0) ? fmaf(__fmul_rn(k45, cj), cj, a0) : a0);
+    anti = __fmul_rn(ow3, cj);
 }
 
 // Post-collision values of the opposite pair (i, opp i) from the pair's even
@@ -163,13 +198,18 @@ __device__ __forceinline__ void moments(const float (&f)[L::Q], float& dr, float
 __device__ __forceinline__ void pair_relax(float fi, float fo, float sym, float anti, float omc, float hw,
                                            float hwm, bool trt, float& oi, float& oo) {
     if (!trt) {
-        oi = fmaf(omc, fi, sym + anti);
-        oo = fmaf(omc, fo, sym - anti);
+        oi = fmaf(omc, fi, __fadd_rn(sym, anti));
+        oo = fmaf(omc, fo, __fsub_rn(sym, anti));
     } else {
-        const float hp = hw * (fi + fo), hm = hwm * (fi - fo);
-        oi = (fi - hp - hm) + (sym + anti);
-        oo = (fo - hp + hm) + (sym - anti);
+        const float hp = __fmul_rn(hw, __fadd_rn(fi, fo)), hm = __fmul_rn(hwm, __fsub_rn(fi, fo));
+        oi = __fadd_rn(__fsub_rn(__fsub_rn(fi, hp), hm), __fadd_rn(sym, anti));
+        oo = __fadd_rn(__fadd_rn(__fsub_rn(fo, hp), hm), __fsub_rn(sym, anti));
     }
+}
+// Running sum of f_i - f*_i over the pairs, for the mass-balanced rest
+// population f*_0 = f_0 + sum_{i != 0} (f_i - f*_i).
+__device__ __forceinline__ float pair_dsum(float dsum, float fi, float fo, float oi, float oo) {
+    return __fadd_rn(dsum, __fadd_rn(__fsub_rn(fi, oi), __fsub_rn(fo, oo)));
 }
 
 template <int I, class L>

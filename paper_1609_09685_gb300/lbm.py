@@ -61,6 +61,7 @@ class lbm_options(C.Structure):
         ("in_place_pairs", C.c_int32),
         ("collision", C.c_int32),
         ("trt_lambda", C.c_double),
+        ("tile_rows", C.c_int32),
     ]
 
 
@@ -176,7 +177,7 @@ def current_stream() -> Optional[int]:
 def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=200,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
-                 in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0) -> lbm_options:
+                 in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0, tile_rows=0) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -193,6 +194,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.in_place_pairs = 1 if in_place_pairs else 0
     o.collision = collision
     o.trt_lambda = trt_lambda
+    o.tile_rows = tile_rows
     return o
 
 

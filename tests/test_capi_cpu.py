@@ -189,3 +189,11 @@ def test_readme_c_example_compiles(lib, tmp_path):
                         str(tmp_path / "example"), "-L", libdir, "-llbm_gb300", f"-Wl,-rpath,{libdir}"],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_tile_rows_option_is_validated(lib):
+    m = np.zeros((6, 9), np.uint8)
+    h = C.c_void_p()
+    for rows in (-2, 5):
+        o = lbm.make_options(tile_rows=rows)
+        assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
