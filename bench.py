@@ -58,6 +58,8 @@ def parse():
                    help="also run the paper's force-driven periodic 3D experiment (100^3, phi 0.748587)")
     p.add_argument("--local-kn", action="store_true",
                    help="also time the local pore-size / local-Kn pass over every domain")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default launch configuration instead of running the library's autotuner")
     p.add_argument("--tile-rows", type=int, default=0,
                    help="gather step: rows per staged tile (1..4), -1 = direct loads, 0 = library default")
     p.add_argument("--collision", choices=["bgk", "trt"], default="bgk",
@@ -541,7 +543,8 @@ def kernel_table(kt, steps, bytes_per_launch, peak, workload, q):
     return kernels
 
 
-def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak, peak_src, tile_rows=0):
+def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak, peak_src, tile_rows=0,
+                autotune=True):
     """Per-kernel rooflines of a second workload, timed like the headline one
     (used for the D3Q19 256x128x128 configuration)."""
     wl = get_workload(wl_name, 0)
@@ -551,6 +554,7 @@ def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak,
     s = lbm.lbm_batch_create(masks, [d.tau for d in wl.domains], [d.drho for d in wl.domains], opts)
     fluid = s.fluid_nodes
     bpl = 2 * 4 * q * fluid
+    tune = lbm.lbm_autotune(s) if autotune else None
     t, t_kern, _, kt, _ = time_intervals(lbm, s, stream, N, steps, warmup, barrier)
     s.close()
     kernels = kernel_table(kt, steps, bpl, peak, wl_name, q)
@@ -564,7 +568,8 @@ def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak,
             "algorithmic_bytes": f"{2 * 4 * q} B per fluid-node update (one step)",
             "avg_launch_us": dk["avg_launch_us"], "peak_source": peak_src, "kernels": kernels,
             "plain_step_average": {"avg_step_us": t_kern * 1e6, "achieved": ach, "frac": ach / peak,
-                                   "timing": "CUDA events around the graph-launched plain steps"}}
+                                   "timing": "CUDA events around the graph-launched plain steps"},
+            "autotune": tune}
 
 
 def run_native(args):
@@ -597,6 +602,9 @@ def run_native(args):
     s = lbm.lbm_batch_create(masks, taus, drhos, opts)
     fluid = s.fluid_nodes
     bytes_per_launch = 2 * 4 * q * fluid
+    tune = None
+    if not args.no_autotune and args.tile_rows == 0:
+        tune = lbm.lbm_autotune(s)  # CUDA-event timing of every candidate on this solver's stream
 
     def barrier():
         torch.cuda.synchronize()
@@ -623,6 +631,11 @@ def run_native(args):
     h2d = sum(m.nbytes for m in pinned) + 48 * len(pinned) + 4 * (len(pinned) + 1)
     nseg = sum(((d.nx + 31) // 32) * d.ny * d.nz for d in wl.domains)
     d2h = 4 * nseg + 4 + 8 * lbm.NUM_OBS * len(pinned)
+    if tune is not None:  # the end-to-end solvers take the tuned configuration through their options
+        c = tune["chosen"]
+        opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, block_threads=c["block_threads"],
+                                strip_rows=c["strip_rows"], gather_batch=c["gather_batch"],
+                                tile_rows=c["tile_rows"])
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -654,7 +667,7 @@ def run_native(args):
     roof3 = None
     if rank == 0 and not args.no_d3q19 and q == 9:
         roof3 = roofline_of(lbm, "d3q19", sp, stream, N, args.steps, args.warmup, coll, torch.cuda.synchronize,
-                            peak, peak_src, args.tile_rows)
+                            peak, peak_src, args.tile_rows, not args.no_autotune)
     ttp = measure_ttp(args, lbm, sp) if (not args.no_ttp and rank == 0) else None
     f3d = measure_forced3d(lbm, sp) if (args.forced3d and rank == 0) else None
     kns = measure_kn_sweep(lbm, sp) if (args.kn_sweep and rank == 0) else None
@@ -700,6 +713,7 @@ def run_native(args):
             "e2e": {"value": e2e_updates / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "step": "create from pinned host masks + one interval + permeability readback"},
+            "autotune": tune,
             "gpu_launches": args.steps * (sum(kt[k][1] for k in kinds) // args.steps + 2),
             "ms_per_step_per_kernel_pass": t_prof / args.steps * 1e3,
             "clocks": clocks,

@@ -94,6 +94,11 @@ typedef struct lbm_options {
                                 tiles of this many rows x 128 nodes (bulk copies by a producer warp, consumed by
                                 four compute warps); 0 or -1 = direct loads per strip (the default, faster on
                                 GB300; D3Q19 always direct).  Every choice gives bit-identical results. */
+    int32_t gather_batch;    /* rows of loads in flight per warp of the direct gather step: 2 or 4 (D2Q9), 1 or 2
+                                (D3Q19); 0 = default (4 / 2).  Bit-identical results either way. */
+    int32_t autotune;        /* 1: run lbm_autotune at creation (with tune_cache); 0 (default): keep the launch
+                                configuration given by the fields above, i.e. force the defaults */
+    const char* tune_cache;  /* JSON cache file of lbm_autotune (NULL: none); read and updated */
 } lbm_options;
 
 /* One domain of a batch. */
@@ -230,6 +235,69 @@ void lbm_batch_destroy(lbm_batch b);
  * blocks stay cached there for the next solver, the rest returns to the
  * CUDA driver at the next synchronisation. */
 void lbm_destroy(lbm_handle h);
+
+/*
+ * Launch configuration of the plain steps, and the runtime autotuner.  The
+ * paper has no counterpart: these choose how the step of Sec. 2 is mapped onto
+ * the GPU, never what it computes -- every configuration gives bit-identical
+ * populations.
+ *   block_threads  block size of the gather, local and pull steps (32..256, a
+ *                  multiple of 32)
+ *   strip_rows     rows per work item of the pull and direct gather steps (1..255)
+ *   gather_batch   rows of loads a warp of the direct gather step keeps in
+ *                  flight: 2 or 4 (D2Q9), 1 or 2 (D3Q19)
+ *   tile_rows      0: direct gather step; 1..4: staged gather step (D2Q9)
+ * lbm_get_launch reports the solver's configuration; lbm_set_launch changes
+ * it (LBM_ERR_ARG for a value outside the ranges above).
+ */
+typedef struct lbm_launch {
+    int32_t block_threads, strip_rows, gather_batch, tile_rows;
+} lbm_launch;
+lbm_status lbm_get_launch(lbm_handle h, lbm_launch* cfg);
+lbm_status lbm_set_launch(lbm_handle h, const lbm_launch* cfg);
+/* Device time per plain step: nsteps (even, 2..10000) plain steps of every
+ * active domain, launched one by one on the solver's stream, timed with CUDA
+ * events after two warm-up steps.  The populations are saved before and
+ * restored after, and the step counter does not move.  Synchronises. */
+lbm_status lbm_time_steps(lbm_handle h, int32_t nsteps, double* us_per_step);
+
+/*
+ * Autotuner.  Times each candidate configuration with lbm_time_steps (nsteps
+ * per candidate, 0 = 20) and keeps the fastest; the candidates are block size
+ * {64, 128, 256} x strip rows {4, 8, 16} x gather batch (both compiled ones),
+ * plus the staged gather step with 2 and 3 tile rows for D2Q9.  With
+ * cache_path (nullable), the choice is looked up first under the key of
+ * lbm_tune_key and stored after a search.  Force-driven solvers have nothing
+ * to tune (their steps are pull steps of their own kernel): the call only
+ * reports their configuration.  out (nullable) receives the chosen and the
+ * default configuration with their times per plain step, the number of
+ * configurations timed (0 when the cache answered) and whether it did.
+ */
+typedef struct lbm_tune_result {
+    lbm_launch chosen;
+    double us_per_step;
+    lbm_launch defaults;
+    double us_per_step_default;
+    int32_t candidates;
+    int32_t from_cache;
+} lbm_tune_result;
+lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lbm_tune_result* out);
+/* Cache key of a solver: "<device>|q<Q>|n2^<b>|eq<e>|coll<c>|<kernel hash>",
+ * b = floor(log2(fluid nodes)), spaces of the device name replaced by '_',
+ * the kernel hash that of the library's CUDA sources.  lbm_tune_key_for
+ * builds the same key from its parts (host only).  LBM_ERR_ARG if cap is too
+ * small. */
+lbm_status lbm_tune_key(lbm_handle h, char* key, size_t cap);
+lbm_status lbm_tune_key_for(const char* device_name, int32_t q, int64_t fluid_nodes, int32_t eq,
+                            int32_t collision, char* key, size_t cap);
+/* The cache file: a JSON object with one member per key, each an object with
+ * the four lbm_launch fields and "us_per_step".  lbm_tune_cache_get sets
+ * *found to 1 and fills cfg / us_per_step (nullable) when key is present
+ * (a missing or unreadable file counts as empty); lbm_tune_cache_put adds or
+ * replaces key and rewrites the file (LBM_ERR_IO if it cannot).  Host only. */
+lbm_status lbm_tune_cache_get(const char* path, const char* key, lbm_launch* cfg, double* us_per_step,
+                              int32_t* found);
+lbm_status lbm_tune_cache_put(const char* path, const char* key, const lbm_launch* cfg, double us_per_step);
 
 /* Number of domains, lattice size Q, and fluid node count of domain d. */
 lbm_status lbm_info(lbm_handle h, int32_t* n_domains, int32_t* q, int64_t* fluid_nodes_total);

@@ -30,9 +30,22 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def kernel_hash() -> str:
+    """Hash of the CUDA sources and the C header: the autotuner's cache key
+    carries it, so a cached launch configuration is dropped when a kernel
+    changes."""
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*.cu*")) + glob.glob(os.path.join(CSRC, "*.h")) +
+                    [os.path.join(INCLUDE, "lbm.h")]):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _flags(defines=()):
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-I", INCLUDE, "-I", CSRC] + [f"-D{d}" for d in defines]
+                   "-I", INCLUDE, "-I", CSRC, f'-DLBM_KERNEL_HASH="{kernel_hash()}"'] + [f"-D{d}" for d in defines]
 
 
 def _stamp(srcs, defines=()):

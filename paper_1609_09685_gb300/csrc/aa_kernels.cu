@@ -307,18 +307,20 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
     }
 }
 template <class L>
-constexpr size_t gather_smem_bytes(int threads) {
-    return GatherSmem<L>::on ? (size_t)(threads / 32) * GatherSmem<L>::rows * L::Q * 32 * sizeof(uint32_t) : 0;
+constexpr size_t gather_smem_bytes(int threads, int rs) {
+    return GatherSmem<L>::on ? (size_t)(threads / 32) * (size_t)rs * L::Q * 32 * sizeof(uint32_t) : 0;
 }
 
-template <class L, int EQ>
+// RS: rows of loads a warp keeps in flight (the "gather batch" of a launch
+// configuration); 0 selects the default of the lattice.
+template <class L, int EQ, int RS>
 __global__ void __maxnreg__(LBM_AA_GATHER_REGS_2D) k_aa_gather2(const __grid_constant__ HotArgs A) {
-    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, GatherSmem<L>::rows>(A);
+    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, RS>(A);
     else aa_gather_body<L, EQ>(A);
 }
-template <class L, int EQ>
+template <class L, int EQ, int RS>
 __global__ void __maxnreg__(LBM_AA_GATHER_REGS_3D) k_aa_gather3(const __grid_constant__ HotArgs A) {
-    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, GatherSmem<L>::rows>(A);
+    if constexpr (GatherSmem<L>::on) aa_gather_smem_body<L, EQ, RS>(A);
     else aa_gather_body<L, EQ>(A);
 }
 
@@ -829,59 +831,76 @@ static cudaError_t staged_dispatch(int rows, const HotArgs& A, cudaStream_t st) 
     return cudaErrorInvalidValue;
 }
 
-template <class L, int EQ>
-static cudaError_t aa_half_launch(int half, int threads, int tile_rows, const HotArgs& A, cudaStream_t st) {
-    if (half == 0 && tile_rows > 0) return staged_dispatch<L, EQ>(tile_rows, A, st);
-    if (half == 0) {
-        const unsigned nb = aa_blocks(A.nitems, threads);
-        if (nb == 0) return cudaSuccess;
-        void (*kern)(HotArgs);
-        if constexpr (L::Q == 9) kern = k_aa_gather2<L, EQ>;
-        else kern = k_aa_gather3<L, EQ>;
-        const size_t sm = gather_smem_bytes<L>(threads);
-        if (GatherSmem<L>::on) {
-            // a function attribute is per device: set it once on each
-            static std::atomic<uint64_t> attr_set{0};  // bit d: set on device d (per template instance)
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
+// Row batches of the direct gather step a launch configuration may choose.
+template <class L>
+struct GatherBatches {
+    static constexpr int lo = (L::Q == 9) ? 2 : 1, hi = (L::Q == 9) ? 4 : 2;
+};
+
+template <class L, int EQ, int RS>
+static cudaError_t gather_direct_launch(int threads, const HotArgs& A, cudaStream_t st) {
+    const unsigned nb = aa_blocks(A.nitems, threads);
+    if (nb == 0) return cudaSuccess;
+    void (*kern)(HotArgs);
+    if constexpr (L::Q == 9) kern = k_aa_gather2<L, EQ, RS>;
+    else kern = k_aa_gather3<L, EQ, RS>;
+    const size_t sm = gather_smem_bytes<L>(threads, RS);
+    if (GatherSmem<L>::on) {
+        // a function attribute is per device: set it once on each
+        static std::atomic<uint64_t> attr_set{0};  // bit d: set on device d (per template instance)
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const uint64_t bit = 1ull << (dev & 63);
+        if (dev >= 64 || !(attr_set.load() & bit)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)gather_smem_bytes<L>(256, RS));
             if (e != cudaSuccess) return e;
-            const uint64_t bit = 1ull << (dev & 63);
-            if (dev >= 64 || !(attr_set.load() & bit)) {
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gather_smem_bytes<L>(256));
-                if (e != cudaSuccess) return e;
-                if (dev < 64) attr_set.fetch_or(bit);
-            }
+            if (dev < 64) attr_set.fetch_or(bit);
         }
-        kern<<<nb, threads, sm, st>>>(A);
-        return cudaGetLastError();
+    }
+    kern<<<nb, threads, sm, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <class L, int EQ>
+static cudaError_t aa_half_launch(int half, const StepLaunch& cfg, const HotArgs& A, cudaStream_t st) {
+    const int threads = cfg.threads > 0 ? cfg.threads : 128;
+    if (half == 0 && cfg.tile_rows > 0) return staged_dispatch<L, EQ>(cfg.tile_rows, A, st);
+    if (half == 0) {
+        const int rs = cfg.gather_batch > 0 ? cfg.gather_batch : GatherSmem<L>::rows;
+        if (rs == GatherBatches<L>::lo) return gather_direct_launch<L, EQ, GatherBatches<L>::lo>(threads, A, st);
+        if (rs == GatherBatches<L>::hi) return gather_direct_launch<L, EQ, GatherBatches<L>::hi>(threads, A, st);
+        return cudaErrorInvalidValue;
     }
     const unsigned nv = aa_blocks(A.nvitems, threads);
     if (nv > 0) k_aa_local<L, EQ><<<nv, threads, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, int threads, int tile_rows,
-                           cudaStream_t st) {
-    if (threads <= 0) threads = 128;
+cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st) {
     for (int i = 0; i < 19; ++i) {
         A.dst[i] = i < q ? g + (size_t)i * A.pstride : nullptr;
         A.src[i] = A.dst[i];
     }
     if (q == 9)
-        return eq == 0 ? aa_half_launch<D2Q9, 0>(half, threads, tile_rows, A, st)
-                       : aa_half_launch<D2Q9, 1>(half, threads, tile_rows, A, st);
-    return eq == 0 ? aa_half_launch<D3Q19, 0>(half, threads, tile_rows, A, st)
-                   : aa_half_launch<D3Q19, 1>(half, threads, tile_rows, A, st);
+        return eq == 0 ? aa_half_launch<D2Q9, 0>(half, cfg, A, st) : aa_half_launch<D2Q9, 1>(half, cfg, A, st);
+    return eq == 0 ? aa_half_launch<D3Q19, 0>(half, cfg, A, st) : aa_half_launch<D3Q19, 1>(half, cfg, A, st);
 }
 
-cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, int tile_rows, cudaStream_t st) {
-    cudaError_t e = launch_aa_half(q, eq, 0, A, g, threads, tile_rows, st);
+cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st) {
+    cudaError_t e = launch_aa_half(q, eq, 0, A, g, cfg, st);
     if (e != cudaSuccess) return e;
-    return launch_aa_half(q, eq, 1, A, g, threads, tile_rows, st);
+    return launch_aa_half(q, eq, 1, A, g, cfg, st);
 }
 
 int staged_gather_lattice(int q) { return q == 9; }
+
+void gather_batches(int q, int* lo, int* hi, int* def) {
+    *lo = q == 9 ? GatherBatches<D2Q9>::lo : GatherBatches<D3Q19>::lo;
+    *hi = q == 9 ? GatherBatches<D2Q9>::hi : GatherBatches<D3Q19>::hi;
+    *def = q == 9 ? GatherSmem<D2Q9>::rows : GatherSmem<D3Q19>::rows;
+}
 
 int local_step_vector(int q) { return q == 9 ? LocalVec<D2Q9>::value : LocalVec<D3Q19>::value; }
 

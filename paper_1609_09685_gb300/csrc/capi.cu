@@ -92,6 +92,9 @@ struct lbm_solver {
     GatherTile* d_tiles = nullptr;  // staged gather step: tile list
     uint32_t ntiles = 0;
     int tile_rows = 0;              // rows per tile of the staged gather step (0: direct gather step)
+    int gather_batch = 0;           // rows in flight per warp of the direct gather step (0: default)
+    int strip_rows = 8;             // rows per strip work item
+    std::vector<uint32_t> h_off, h_smask;  // segment offsets and fluid masks (host copies)
     bool forced = false;         // force-driven, every face periodic (lbm_batch_create_forced)
     bool obs_only = false;       // the last observation was taken without stepping
     float* d_gforce = nullptr;   // body acceleration per domain (force-driven solvers)
@@ -119,6 +122,7 @@ struct lbm_solver {
         G.pstride = pstride;
         return G;
     }
+    StepLaunch launch_cfg() const { return StepLaunch{opt.block_threads, tile_rows, gather_batch}; }
     HotArgs hot() const {
         HotArgs A;
         A.dom = d_dom;
@@ -315,13 +319,12 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     } else if (h->opt.in_place_pairs) {
         for (; plain >= 2; plain -= 2) {
             if (!prof) {
-                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->opt.block_threads, h->tile_rows, h->st));
+                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->launch_cfg(), h->st));
                 continue;
             }
             for (int half = 0; half < 2; ++half) {
                 CK(h, prof->mark(h->st));
-                CK(h, launch_aa_half(h->q, h->eq, half, A, h->d_g[h->cur], h->opt.block_threads, h->tile_rows,
-                                     h->st));
+                CK(h, launch_aa_half(h->q, h->eq, half, A, h->d_g[h->cur], h->launch_cfg(), h->st));
                 CK(h, prof->mark(h->st));
                 prof->kind.push_back(half);
             }
@@ -600,6 +603,106 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
     return rs;
 }
 
+namespace {
+
+// Strip work list of the pull and direct gather steps: per domain and z
+// plane, runs of up to R rows at each segment column, with the column
+// innermost so that warps of one block (and neighbouring blocks) sweep
+// adjacent segments of the same rows -- contiguous compact ranges in every
+// population plane.  Strips whose segments are all solid are left out.  Sets
+// each domain's item range and uploads the list and the domain records.
+lbm_status build_items(lbm_handle h, int R) {
+    const int n = (int)h->dom.size();
+    const std::vector<uint32_t>& smask = h->h_smask;
+    std::vector<uint4> items;
+    for (int d = 0; d < n; ++d) {
+        DomainDev& G = h->hdom[d];
+        G.item_base = (uint32_t)items.size();
+        for (int z = 0; z < G.nz; ++z)
+            for (int y0 = 0; y0 < G.ny; y0 += R)
+                for (int sidx = 0; sidx < G.nseg; ++sidx) {
+                    const int nr = std::min(R, G.ny - y0);
+                    const uint32_t g0 = G.seg_base + ((uint32_t)z * G.ny + y0) * G.nseg + sidx;
+                    bool any = false;
+                    for (int k = 0; k < nr && !any; ++k) any = smask[g0 + (uint32_t)k * G.nseg] != 0u;
+                    if (!any) continue;
+                    items.push_back(make_uint4(g0, (uint32_t)d | ((uint32_t)nr << 24),
+                                               (uint32_t)y0 | ((uint32_t)z << 16), (uint32_t)sidx));
+                }
+        G.nitems = (uint32_t)items.size() - G.item_base;
+    }
+    dfree(h, h->d_items);
+    h->nitems = (uint32_t)items.size();
+    CK(h, dmalloc(h, &h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
+    CK(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
+    for (int d = 0; d < n; ++d) h->hdom[d].active = h->dom[d].active;
+    CK(h, cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    h->strip_rows = R;
+    return LBM_OK;
+}
+
+// Tiles of the staged gather step (D2Q9 in-place pairs): per domain and z
+// plane, tr rows x kTileSegs segment columns, column groups innermost;
+// all-solid tiles are left out.  For each source row (the rows above and
+// below included, clamped onto the domain) the 16-byte aligned compact range
+// that covers nodes 32 s0 - 1 .. 32 (s0 + nsegs).  tr = 0 drops the list
+// (direct gather step).
+lbm_status build_tiles(lbm_handle h, int tr) {
+    const int n = (int)h->dom.size();
+    if (tr && (h->q != 9 || !h->opt.in_place_pairs || h->forced)) tr = 0;
+    for (int d = 0; d < n && tr; ++d)
+        if (h->hdom[d].nseg > 65535) tr = 0;  // s0 is packed in 16 bits
+    const std::vector<uint32_t>& smask = h->h_smask;
+    const std::vector<uint32_t>& off = h->h_off;
+    std::vector<GatherTile> tiles;
+    for (int d = 0; d < n && tr; ++d) {
+        const DomainDev& G = h->hdom[d];
+        for (int z = 0; z < G.nz; ++z)
+            for (int y0 = 0; y0 < G.ny; y0 += tr)
+                for (int s0 = 0; s0 < G.nseg; s0 += kTileSegs) {
+                    const int nr = std::min(tr, G.ny - y0), ns = std::min(kTileSegs, G.nseg - s0);
+                    auto seg = [&](int y, int sx) {
+                        return G.seg_base + ((uint32_t)z * G.ny + (uint32_t)y) * (uint32_t)G.nseg + (uint32_t)sx;
+                    };
+                    bool any = false;
+                    for (int r = 0; r < nr && !any; ++r)
+                        for (int k = 0; k < ns && !any; ++k) any = smask[seg(y0 + r, s0 + k)] != 0u;
+                    if (!any) continue;
+                    GatherTile T{};
+                    T.dom = (uint32_t)d;
+                    T.yz = (uint32_t)y0 | ((uint32_t)z << 16);
+                    T.shape = (uint32_t)nr | ((uint32_t)ns << 8) | ((uint32_t)s0 << 16);
+                    T.dims = (uint32_t)G.ny | ((uint32_t)G.nseg << 16);
+                    T.wbase = seg(0, s0);
+                    for (int qq = 0; qq < nr + 2; ++qq) {
+                        const int yc = std::min(std::max(y0 - 1 + qq, 0), G.ny - 1);
+                        const uint32_t g0 = seg(yc, s0), g1 = seg(yc, s0 + ns - 1);
+                        const uint32_t left = s0 > 0 ? (smask[g0 - 1] >> 31) & 1u : 0u;
+                        const uint32_t right = s0 + ns < G.nseg ? smask[g1 + 1] & 1u : 0u;
+                        const uint32_t lo = off[g0] - left;
+                        const uint32_t hi = off[g1] + (uint32_t)__builtin_popcount(smask[g1]) + right;
+                        const uint32_t a0 = lo & ~3u, a1 = (hi + 3u) & ~3u;
+                        T.a0[qq] = a0;
+                        T.n16[qq] = (uint16_t)(hi > lo ? (a1 - a0) / 4u : 0u);
+                    }
+                    tiles.push_back(T);
+                }
+    }
+    dfree(h, h->d_tiles);
+    h->tile_rows = tr;
+    h->ntiles = (uint32_t)tiles.size();
+    if (tr) {
+        CK(h, dmalloc(h, &h->d_tiles, sizeof(GatherTile) * std::max<size_t>(tiles.size(), 1)));
+        CK(h, cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(GatherTile) * tiles.size(), cudaMemcpyHostToDevice,
+                              h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
 static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, int force_q,
                               lbm_handle* out, const double* gforce = nullptr) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
@@ -617,7 +720,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         o.block_threads > 256 || (o.block_threads % 32) != 0 || o.strip_rows < 0 || o.strip_rows > 255 ||
         (o.in_place_pairs != 0 && o.in_place_pairs != 1) ||
         (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
-        !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax)
+        !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax ||
+        (o.autotune != 0 && o.autotune != 1) || o.gather_batch < 0)
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (gforce) {
         o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
@@ -771,86 +875,27 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         CKC(cudaMemcpyAsync(h->d_vitems, vit.data(), sizeof(uint2) * vit.size(), cudaMemcpyHostToDevice, h->st));
         CKC(cudaStreamSynchronize(h->st));
     }
-    // Strip work list: per domain and z plane, runs of up to R rows at each
-    // segment column, with the column innermost so that warps of one block (and
-    // neighbouring blocks) sweep adjacent segments of the same rows -- contiguous
-    // compact ranges in every population plane.  Strips whose segments are all
-    // solid are left out.
-    const int R = o.strip_rows > 0 ? o.strip_rows : 8;
-    std::vector<uint4> items;
-    for (int d = 0; d < n; ++d) {
-        DomainDev& G = h->hdom[d];
-        G.item_base = (uint32_t)items.size();
-        for (int z = 0; z < G.nz; ++z)
-            for (int y0 = 0; y0 < G.ny; y0 += R)
-                for (int sidx = 0; sidx < G.nseg; ++sidx) {
-                    const int nr = std::min(R, G.ny - y0);
-                    const uint32_t g0 = G.seg_base + ((uint32_t)z * G.ny + y0) * G.nseg + sidx;
-                    bool any = false;
-                    for (int k = 0; k < nr && !any; ++k) any = smask[g0 + (uint32_t)k * G.nseg] != 0u;
-                    if (!any) continue;
-                    items.push_back(make_uint4(g0, (uint32_t)d | ((uint32_t)nr << 24),
-                                               (uint32_t)y0 | ((uint32_t)z << 16), (uint32_t)sidx));
-                }
-        G.nitems = (uint32_t)items.size() - G.item_base;
-    }
-    h->nitems = (uint32_t)items.size();
-    // Tiles of the staged gather step (D2Q9 in-place pairs): per domain and z
-    // plane, TR rows x kTileSegs segment columns, column groups innermost;
-    // all-solid tiles are left out.  For each source row (the rows above and
-    // below included, clamped onto the domain) the 16-byte aligned compact
-    // range that covers nodes 32 s0 - 1 .. 32 (s0 + nsegs).
     {
-        int tr = 0;
-        if (q == 9 && o.in_place_pairs && !gforce && o.tile_rows > 0) tr = o.tile_rows;
-        for (int d = 0; d < n && tr; ++d)
-            if (h->hdom[d].nseg > 65535) tr = 0;  // s0 is packed in 16 bits
-        std::vector<GatherTile> tiles;
-        for (int d = 0; d < n && tr; ++d) {
-            const DomainDev& G = h->hdom[d];
-            for (int z = 0; z < G.nz; ++z)
-                for (int y0 = 0; y0 < G.ny; y0 += tr)
-                    for (int s0 = 0; s0 < G.nseg; s0 += kTileSegs) {
-                        const int nr = std::min(tr, G.ny - y0), ns = std::min(kTileSegs, G.nseg - s0);
-                        auto seg = [&](int y, int sx) {
-                            return G.seg_base + ((uint32_t)z * G.ny + (uint32_t)y) * (uint32_t)G.nseg + (uint32_t)sx;
-                        };
-                        bool any = false;
-                        for (int r = 0; r < nr && !any; ++r)
-                            for (int k = 0; k < ns && !any; ++k) any = smask[seg(y0 + r, s0 + k)] != 0u;
-                        if (!any) continue;
-                        GatherTile T{};
-                        T.dom = (uint32_t)d;
-                        T.yz = (uint32_t)y0 | ((uint32_t)z << 16);
-                        T.shape = (uint32_t)nr | ((uint32_t)ns << 8) | ((uint32_t)s0 << 16);
-                        T.dims = (uint32_t)G.ny | ((uint32_t)G.nseg << 16);
-                        T.wbase = seg(0, s0);
-                        for (int qq = 0; qq < nr + 2; ++qq) {
-                            const int yc = std::min(std::max(y0 - 1 + qq, 0), G.ny - 1);
-                            const uint32_t g0 = seg(yc, s0), g1 = seg(yc, s0 + ns - 1);
-                            const uint32_t left = s0 > 0 ? (smask[g0 - 1] >> 31) & 1u : 0u;
-                            const uint32_t right = s0 + ns < G.nseg ? smask[g1 + 1] & 1u : 0u;
-                            const uint32_t lo = off[g0] - left;
-                            const uint32_t hi = off[g1] + (uint32_t)__builtin_popcount(smask[g1]) + right;
-                            const uint32_t a0 = lo & ~3u, a1 = (hi + 3u) & ~3u;
-                            T.a0[qq] = a0;
-                            T.n16[qq] = (uint16_t)(hi > lo ? (a1 - a0) / 4u : 0u);
-                        }
-                        tiles.push_back(T);
-                    }
+        int lo, hi, def;
+        gather_batches(q, &lo, &hi, &def);
+        if (o.gather_batch != 0 && o.gather_batch != lo && o.gather_batch != hi) {
+            free_solver(h);
+            *out = nullptr;
+            return fail(nullptr, LBM_ERR_ARG, "gather_batch must be 0 or one of the lattice's compiled batches");
         }
-        h->tile_rows = tr;
-        h->ntiles = (uint32_t)tiles.size();
-        if (tr) {
-            CKC(dmalloc(h, &h->d_tiles, sizeof(GatherTile) * std::max<size_t>(tiles.size(), 1)));
-            CKC(cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(GatherTile) * tiles.size(), cudaMemcpyHostToDevice,
-                                h->st));
-            CKC(cudaStreamSynchronize(h->st));
+        h->gather_batch = o.gather_batch;
+    }
+    h->h_off.assign(off.begin(), off.end() - 1);
+    h->h_smask.assign(smask.begin(), smask.begin() + sb);
+    {
+        lbm_status bs = build_items(h, o.strip_rows > 0 ? o.strip_rows : 8);
+        if (bs == LBM_OK) bs = build_tiles(h, o.tile_rows > 0 ? o.tile_rows : 0);
+        if (bs != LBM_OK) {
+            free_solver(h);
+            *out = nullptr;
+            return bs;
         }
     }
-    CKC(dmalloc(h, &h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
-    CKC(cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
-    CKC(cudaMemcpyAsync(h->d_dom, h->hdom.data(), sizeof(DomainDev) * n, cudaMemcpyHostToDevice, h->st));
     CKC(dmalloc(h, &h->d_win, sizeof(uint4) * std::max<uint32_t>(sb, 1)));
     CKC(launch_build_windows(h->d_dom, h->d_seg_dom, sb, h->d_seg_mask, h->d_seg_off, h->d_win, h->st));
     CKC(cudaStreamSynchronize(h->st));
@@ -864,7 +909,9 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(dmalloc(h, &h->d_g[0], sizeof(float) * q * h->pstride));
     CKC(dmalloc(h, &h->d_g[1], sizeof(float) * q * h->pstride));
     CKC(dmalloc(h, &h->d_uprev, sizeof(float) * D * h->pstride));
-    CKC(dmalloc(h, &h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(std::max(sb, h->nitems), 1)));
+    // partials: one per strip item (at most one per segment, whatever the strip
+    // rows) or one per segment (observation without a step)
+    CKC(dmalloc(h, &h->d_partials, sizeof(double) * kNumObs * std::max<uint32_t>(sb, 1)));
     CKC(dmalloc(h, &h->d_obs, sizeof(double) * (kNumObs * n + 1)));
     CKC(cudaMemsetAsync(h->d_obs, 0, sizeof(double) * (kNumObs * n + 1), h->st));
     if (gforce) {
@@ -880,6 +927,15 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     CKC(launch_init(q, h->geom(), h->d_g[0], h->d_uprev, h->st));
     CKC(cudaStreamSynchronize(h->st));
 #undef CKC
+    if (o.autotune) {
+        lbm_status ts = lbm_autotune(h, o.tune_cache, 0, nullptr);
+        if (ts != LBM_OK) {
+            std::string msg = std::string("autotune at creation: ") + h->err;
+            free_solver(h);
+            *out = nullptr;
+            return fail(nullptr, ts, msg);
+        }
+    }
     return LBM_OK;
 }
 
@@ -1479,6 +1535,287 @@ lbm_status lbm_load(const char* path, const lbm_options* opt, lbm_handle* out) {
     h->cur = 0;
     h->step = step;
     *out = h;
+    return LBM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Launch configuration and autotuner
+// ---------------------------------------------------------------------------
+#ifndef LBM_KERNEL_HASH
+#define LBM_KERNEL_HASH "unversioned"
+#endif
+
+}  // extern "C"
+
+namespace {
+
+lbm_launch current_launch(lbm_handle h) {
+    int lo, hi, def;
+    gather_batches(h->q, &lo, &hi, &def);
+    lbm_launch c;
+    c.block_threads = h->opt.block_threads > 0 ? h->opt.block_threads : 128;
+    c.strip_rows = h->strip_rows;
+    c.gather_batch = h->gather_batch > 0 ? h->gather_batch : def;
+    c.tile_rows = h->tile_rows;
+    return c;
+}
+
+bool launch_valid(lbm_handle h, const lbm_launch& c) {
+    int lo, hi, def;
+    gather_batches(h->q, &lo, &hi, &def);
+    return c.block_threads >= 32 && c.block_threads <= 256 && c.block_threads % 32 == 0 && c.strip_rows >= 1 &&
+           c.strip_rows <= 255 && (c.gather_batch == lo || c.gather_batch == hi) && c.tile_rows >= 0 &&
+           c.tile_rows <= kTileRowsMax && (c.tile_rows == 0 || staged_gather_lattice(h->q));
+}
+
+lbm_status apply_launch(lbm_handle h, const lbm_launch& c) {
+    if (!launch_valid(h, c)) return fail(h, LBM_ERR_ARG, "launch configuration outside the allowed ranges");
+    const lbm_launch cur = current_launch(h);
+    lbm_status s = LBM_OK;
+    if (c.strip_rows != cur.strip_rows) s = build_items(h, c.strip_rows);
+    if (s == LBM_OK && c.tile_rows != cur.tile_rows) s = build_tiles(h, c.tile_rows);
+    if (s != LBM_OK) return s;
+    h->opt.block_threads = c.block_threads;
+    h->gather_batch = c.gather_batch;
+    // cached graphs hold the old launches
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    return LBM_OK;
+}
+
+std::string key_part(const char* s) {
+    std::string r;
+    for (const char* p = s; *p; ++p) r += (*p == ' ' || *p == '"' || *p == '\\' || *p == '|') ? '_' : *p;
+    return r;
+}
+
+lbm_status write_key(const std::string& k, char* key, size_t cap) {
+    if (!key || cap < k.size() + 1) return fail(nullptr, LBM_ERR_ARG, "key buffer too small");
+    std::memcpy(key, k.c_str(), k.size() + 1);
+    return LBM_OK;
+}
+
+std::string make_key(const char* device, int q, int64_t fluid, int eq, int coll) {
+    int b = 0;
+    while ((int64_t(1) << (b + 1)) <= fluid && b < 62) ++b;
+    return key_part(device) + "|q" + std::to_string(q) + "|n2^" + std::to_string(b) + "|eq" + std::to_string(eq) +
+           "|coll" + std::to_string(coll) + "|" + LBM_KERNEL_HASH;
+}
+
+// The cache file holds one member per line:  "KEY": {"block_threads": B, ...},
+struct CacheEntry {
+    lbm_launch c;
+    double us;
+};
+std::map<std::string, CacheEntry> read_cache(const char* path) {
+    std::map<std::string, CacheEntry> m;
+    FILE* fp = path ? std::fopen(path, "r") : nullptr;
+    if (!fp) return m;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), fp)) {
+        const char* a = std::strchr(line, '"');
+        if (!a) continue;
+        const char* b = std::strchr(a + 1, '"');
+        if (!b) continue;
+        const std::string key(a + 1, b);
+        CacheEntry e{};
+        auto field = [&](const char* name, double* v) {
+            const char* f = std::strstr(b, name);
+            if (!f) return false;
+            f = std::strchr(f + std::strlen(name), ':');
+            return f && std::sscanf(f + 1, "%lf", v) == 1;
+        };
+        double bt, sr, gb, tr, us;
+        if (field("\"block_threads\"", &bt) && field("\"strip_rows\"", &sr) && field("\"gather_batch\"", &gb) &&
+            field("\"tile_rows\"", &tr) && field("\"us_per_step\"", &us)) {
+            e.c.block_threads = (int32_t)bt;
+            e.c.strip_rows = (int32_t)sr;
+            e.c.gather_batch = (int32_t)gb;
+            e.c.tile_rows = (int32_t)tr;
+            e.us = us;
+            m[key] = e;
+        }
+    }
+    std::fclose(fp);
+    return m;
+}
+bool write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long)std::chrono::steady_clock::now()
+                                                                            .time_since_epoch()
+                                                                            .count() % 1000000007);
+    FILE* fp = std::fopen(tmp.c_str(), "w");
+    if (!fp) return false;
+    bool ok = std::fprintf(fp, "{\n") > 0;
+    size_t i = 0;
+    for (const auto& kv : m) {
+        const CacheEntry& e = kv.second;
+        ok = ok && std::fprintf(fp,
+                                "\"%s\": {\"block_threads\": %d, \"strip_rows\": %d, \"gather_batch\": %d, "
+                                "\"tile_rows\": %d, \"us_per_step\": %.3f}%s\n",
+                                kv.first.c_str(), e.c.block_threads, e.c.strip_rows, e.c.gather_batch, e.c.tile_rows,
+                                e.us, ++i < m.size() ? "," : "") > 0;
+    }
+    ok = ok && std::fprintf(fp, "}\n") > 0;
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_launch(lbm_handle h, lbm_launch* cfg) {
+    if (!h || !cfg) return fail(h, LBM_ERR_ARG, "null argument");
+    *cfg = current_launch(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_handle h, const lbm_launch* cfg) {
+    if (!h || !cfg) return fail(h, LBM_ERR_ARG, "null argument");
+    return apply_launch(h, *cfg);
+}
+
+lbm_status lbm_time_steps(lbm_handle h, int32_t nsteps, double* us_per_step) {
+    if (!h || !us_per_step) return fail(h, LBM_ERR_ARG, "null argument");
+    if (nsteps < 2 || nsteps > 10000 || (nsteps & 1)) return fail(h, LBM_ERR_ARG, "nsteps must be even, 2..10000");
+    const size_t bytes = sizeof(float) * (size_t)h->q * h->pstride;
+    float* save = nullptr;
+    CK(h, dmalloc(h, &save, bytes));
+    const int cur0 = h->cur;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(save, h->d_g[cur0], bytes, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    lbm_status s = LBM_OK;
+    if (e == cudaSuccess) s = enqueue_steps(h, 2, false);
+    if (e == cudaSuccess && s == LBM_OK) e = cudaEventRecord(e0, h->st);
+    if (e == cudaSuccess && s == LBM_OK) s = enqueue_steps(h, nsteps, false);
+    if (e == cudaSuccess && s == LBM_OK) e = cudaEventRecord(e1, h->st);
+    if (e == cudaSuccess && s == LBM_OK) e = cudaStreamSynchronize(h->st);
+    float ms = 0.f;
+    if (e == cudaSuccess && s == LBM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    // restore the state (an even number of steps leaves the current buffer in place)
+    h->cur = cur0;
+    cudaError_t e2 = cudaMemcpyAsync(h->d_g[cur0], save, bytes, cudaMemcpyDeviceToDevice, h->st);
+    cudaFreeAsync(save, h->st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s != LBM_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbm_time_steps");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "lbm_time_steps restore");
+    uint32_t word = 0;
+    CK(h, cudaMemcpy(&word, h->err_word(), sizeof(word), cudaMemcpyDeviceToHost));
+    s = device_error(h, word);
+    if (s != LBM_OK) return s;
+    *us_per_step = 1e3 * (double)ms / nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_tune_key_for(const char* device_name, int32_t q, int64_t fluid_nodes, int32_t eq, int32_t collision,
+                            char* key, size_t cap) {
+    if (!device_name) return fail(nullptr, LBM_ERR_ARG, "null device name");
+    return write_key(make_key(device_name, q, fluid_nodes, eq, collision), key, cap);
+}
+
+lbm_status lbm_tune_key(lbm_handle h, char* key, size_t cap) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    int dev = 0;
+    cudaDeviceProp prop{};
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaGetDeviceProperties(&prop, dev));
+    return write_key(make_key(prop.name, h->q, (int64_t)h->nfluid, h->eq, h->opt.collision), key, cap);
+}
+
+lbm_status lbm_tune_cache_get(const char* path, const char* key, lbm_launch* cfg, double* us_per_step,
+                              int32_t* found) {
+    if (!path || !key || !found) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    const auto m = read_cache(path);
+    const auto it = m.find(key);
+    *found = it != m.end();
+    if (*found) {
+        if (cfg) *cfg = it->second.c;
+        if (us_per_step) *us_per_step = it->second.us;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_tune_cache_put(const char* path, const char* key, const lbm_launch* cfg, double us_per_step) {
+    if (!path || !key || !cfg) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    if (std::strchr(key, '"') || std::strchr(key, '\n')) return fail(nullptr, LBM_ERR_ARG, "key holds a quote or newline");
+    auto m = read_cache(path);
+    m[key] = CacheEntry{*cfg, us_per_step};
+    if (!write_cache(path, m)) return fail(nullptr, LBM_ERR_IO, std::string("cannot write ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lbm_tune_result* out) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (nsteps < 0 || nsteps > 10000) return fail(h, LBM_ERR_ARG, "nsteps must be in [0, 10000]");
+    const int steps = nsteps == 0 ? 20 : (nsteps + 1) / 2 * 2;
+    int lo, hi, def;
+    gather_batches(h->q, &lo, &hi, &def);
+    lbm_tune_result r{};
+    r.defaults = lbm_launch{128, 8, def, 0};
+    r.chosen = current_launch(h);
+    if (h->forced) {  // pull steps of the periodic kernel only: nothing to choose
+        if (out) *out = r;
+        return LBM_OK;
+    }
+    char key[512];
+    lbm_status s = lbm_tune_key(h, key, sizeof(key));
+    if (s != LBM_OK) return s;
+    if (cache_path) {
+        const auto m = read_cache(cache_path);
+        const auto it = m.find(key);
+        if (it != m.end() && launch_valid(h, it->second.c)) {
+            s = apply_launch(h, it->second.c);
+            if (s != LBM_OK) return s;
+            r.chosen = it->second.c;
+            r.us_per_step = it->second.us;
+            r.from_cache = 1;
+            if (out) *out = r;
+            return LBM_OK;
+        }
+    }
+    std::vector<lbm_launch> cands{r.defaults};
+    for (int bt : {64, 128, 256})
+        for (int sr : {4, 8, 16})
+            for (int gb : {lo, hi}) {
+                const lbm_launch c{bt, sr, gb, 0};
+                if (std::memcmp(&c, &r.defaults, sizeof(c)) != 0) cands.push_back(c);
+            }
+    if (staged_gather_lattice(h->q) && h->opt.in_place_pairs)
+        for (int tr : {2, 3}) cands.push_back(lbm_launch{128, 8, def, tr});
+    double best = INFINITY;
+    lbm_launch best_c = r.defaults;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        s = apply_launch(h, cands[i]);
+        if (s != LBM_OK) return s;
+        double t = 0.0;
+        s = lbm_time_steps(h, steps, &t);
+        if (s != LBM_OK) return s;
+        if (i == 0) r.us_per_step_default = t;
+        if (t < best) {
+            best = t;
+            best_c = cands[i];
+        }
+    }
+    s = apply_launch(h, best_c);
+    if (s != LBM_OK) return s;
+    r.chosen = best_c;
+    r.us_per_step = best;
+    r.candidates = (int32_t)cands.size();
+    if (cache_path) {
+        s = lbm_tune_cache_put(cache_path, key, &best_c, best);
+        if (s != LBM_OK) return fail(h, s, lbm_last_error(nullptr));
+    }
+    if (out) *out = r;
     return LBM_OK;
 }
 

@@ -11,15 +11,21 @@ namespace lbmgb {
 
 cudaError_t launch_stream_collide(int q, int eq, bool obs, HotArgs A, const float* src, float* dst,
                                   float* uprev, double* partials, int threads, cudaStream_t st);
+// Launch configuration of the plain steps (chosen per solver; every choice
+// gives bit-identical results).
+struct StepLaunch {
+    int threads;       // block size of the direct gather, local and pull steps (0 = 128)
+    int tile_rows;     // > 0: staged gather step over A.tiles (built with that many rows per tile)
+    int gather_batch;  // rows of loads in flight per warp of the direct gather step (0 = default)
+};
 // Two steps in place on g (gather step, then local step); see k_aa_gather.
-// tile_rows > 0 selects the staged gather step over A.tiles (built with that
-// many rows per tile); 0 the direct one over A.items.
-cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, int threads, int tile_rows, cudaStream_t st);
+cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
 // One half of the pair: half 0 = gather step, 1 = local step.
-cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, int threads, int tile_rows,
-                           cudaStream_t st);
+cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
 // Nonzero when the lattice with q directions has a staged gather step.
 int staged_gather_lattice(int q);
+// Row batches of the direct gather step: the two compiled ones and the default.
+void gather_batches(int q, int* lo, int* hi, int* def);
 // Slots per lane of the local step (its work items cover 32 x this many slots).
 int local_step_vector(int q);
 // Inlet/outlet bits of the compact slots (face zeroed beforehand).

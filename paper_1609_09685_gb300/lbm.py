@@ -62,7 +62,23 @@ class lbm_options(C.Structure):
         ("collision", C.c_int32),
         ("trt_lambda", C.c_double),
         ("tile_rows", C.c_int32),
+        ("gather_batch", C.c_int32),
+        ("autotune", C.c_int32),
+        ("tune_cache", C.c_char_p),
     ]
+
+
+class lbm_launch(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("strip_rows", C.c_int32), ("gather_batch", C.c_int32),
+                ("tile_rows", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lbm_tune_result(C.Structure):
+    _fields_ = [("chosen", lbm_launch), ("us_per_step", C.c_double), ("defaults", lbm_launch),
+                ("us_per_step_default", C.c_double), ("candidates", C.c_int32), ("from_cache", C.c_int32)]
 
 
 class lbm_domain_desc(C.Structure):
@@ -118,6 +134,14 @@ def load(path: Optional[str] = None):
         "lbm_batch_permeability": (i32, [P, P]),
         "lbm_batch_destroy": (None, [P]),
         "lbm_lattice": (i32, [i32, P, P, P, P, P]),
+        "lbm_get_launch": (i32, [P, P]),
+        "lbm_set_launch": (i32, [P, P]),
+        "lbm_time_steps": (i32, [P, i32, P]),
+        "lbm_autotune": (i32, [P, C.c_char_p, i32, P]),
+        "lbm_tune_key": (i32, [P, P, C.c_size_t]),
+        "lbm_tune_key_for": (i32, [C.c_char_p, i32, i64, i32, i32, P, C.c_size_t]),
+        "lbm_tune_cache_get": (i32, [C.c_char_p, C.c_char_p, P, P, P]),
+        "lbm_tune_cache_put": (i32, [C.c_char_p, C.c_char_p, P, d]),
         "lbm_get_fields": (i32, [P, i32, P, P, P, P]),
         "lbm_get_populations": (i32, [P, i32, P]),
         "lbm_set_populations": (i32, [P, i32, P]),
@@ -177,7 +201,8 @@ def current_stream() -> Optional[int]:
 def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=200,
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
-                 in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0, tile_rows=0) -> lbm_options:
+                 in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0, tile_rows=0, gather_batch=0,
+                 autotune=False, tune_cache=None) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -195,6 +220,9 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.collision = collision
     o.trt_lambda = trt_lambda
     o.tile_rows = tile_rows
+    o.gather_batch = gather_batch
+    o.autotune = 1 if autotune else 0
+    o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
     return o
 
 
@@ -445,6 +473,59 @@ def lbm_lattice(q: int):
     fz = np.zeros(q, np.int32)
     _check(load().lbm_lattice(int(q), _ptr(c), _ptr(w), _ptr(o), _ptr(fy), _ptr(fz)))
     return c, w, o, fy, fz
+
+
+def lbm_get_launch(s: Solver) -> dict:
+    c = lbm_launch()
+    _check(load().lbm_get_launch(s.handle, C.byref(c)), s.handle)
+    return c.as_dict()
+
+
+def lbm_set_launch(s: Solver, block_threads: int, strip_rows: int, gather_batch: int, tile_rows: int = 0) -> None:
+    c = lbm_launch(block_threads, strip_rows, gather_batch, tile_rows)
+    _check(load().lbm_set_launch(s.handle, C.byref(c)), s.handle)
+
+
+def lbm_time_steps(s: Solver, nsteps: int = 20) -> float:
+    """Device microseconds per plain step (state saved and restored)."""
+    us = C.c_double()
+    _check(load().lbm_time_steps(s.handle, int(nsteps), C.byref(us)), s.handle)
+    return us.value
+
+
+def lbm_autotune(s: Solver, cache_path: Optional[str] = None, nsteps: int = 0) -> dict:
+    r = lbm_tune_result()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().lbm_autotune(s.handle, path, int(nsteps), C.byref(r)), s.handle)
+    return {"chosen": r.chosen.as_dict(), "us_per_step": r.us_per_step, "defaults": r.defaults.as_dict(),
+            "us_per_step_default": r.us_per_step_default, "candidates": r.candidates,
+            "from_cache": bool(r.from_cache)}
+
+
+def lbm_tune_key(s: Solver) -> str:
+    buf = C.create_string_buffer(512)
+    _check(load().lbm_tune_key(s.handle, buf, 512), s.handle)
+    return buf.value.decode()
+
+
+def lbm_tune_key_for(device_name: str, q: int, fluid_nodes: int, eq: int = 0, collision: int = 0) -> str:
+    buf = C.create_string_buffer(512)
+    _check(load().lbm_tune_key_for(device_name.encode(), q, int(fluid_nodes), eq, collision, buf, 512))
+    return buf.value.decode()
+
+
+def lbm_tune_cache_get(path: str, key: str):
+    """(launch dict, us_per_step) or None."""
+    c = lbm_launch()
+    us = C.c_double()
+    found = C.c_int32()
+    _check(load().lbm_tune_cache_get(os.fsencode(path), key.encode(), C.byref(c), C.byref(us), C.byref(found)))
+    return (c.as_dict(), us.value) if found.value else None
+
+
+def lbm_tune_cache_put(path: str, key: str, cfg: dict, us_per_step: float) -> None:
+    c = lbm_launch(cfg["block_threads"], cfg["strip_rows"], cfg["gather_batch"], cfg["tile_rows"])
+    _check(load().lbm_tune_cache_put(os.fsencode(path), key.encode(), C.byref(c), float(us_per_step)))
 
 
 def _shape(s: Solver, d: int):

@@ -197,3 +197,49 @@ def test_tile_rows_option_is_validated(lib):
     for rows in (-2, 5):
         o = lbm.make_options(tile_rows=rows)
         assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+
+
+def test_tune_key_format(lib):
+    """Key = device (spaces -> '_') | Q | floor(log2 fluid nodes) | equilibrium |
+    collision | hash of the kernel sources."""
+    h = build.kernel_hash()
+    assert lbm.lbm_tune_key_for("NVIDIA GB300", 9, 23228319, 0, 0) == f"NVIDIA_GB300|q9|n2^24|eq0|coll0|{h}"
+    assert lbm.lbm_tune_key_for("x", 19, 1 << 24, 1, 1) == f"x|q19|n2^24|eq1|coll1|{h}"
+    assert lbm.lbm_tune_key_for("x", 19, (1 << 24) - 1, 1, 1) == f"x|q19|n2^23|eq1|coll1|{h}"
+    assert lbm.lbm_tune_key_for("x", 9, 1, 0, 0).split("|")[2] == "n2^0"
+    small = C.create_string_buffer(8)
+    assert lib.lbm_tune_key_for(b"NVIDIA GB300", 9, 100, 0, 0, small, 8) == lbm.LBM_ERR_ARG
+
+
+def test_tune_cache_round_trip(lib, tmp_path):
+    path = str(tmp_path / "tune.json")
+    assert lbm.lbm_tune_cache_get(path, "k1") is None  # missing file = empty cache
+    a = dict(block_threads=64, strip_rows=16, gather_batch=2, tile_rows=0)
+    b = dict(block_threads=256, strip_rows=4, gather_batch=4, tile_rows=3)
+    lbm.lbm_tune_cache_put(path, "k1", a, 301.25)
+    lbm.lbm_tune_cache_put(path, "GPU A|q9|n2^20|eq0|coll0|abc", b, 12.5)
+    assert lbm.lbm_tune_cache_get(path, "k1") == (a, 301.25)
+    assert lbm.lbm_tune_cache_get(path, "GPU A|q9|n2^20|eq0|coll0|abc") == (b, 12.5)
+    lbm.lbm_tune_cache_put(path, "k1", b, 99.0)  # replace
+    assert lbm.lbm_tune_cache_get(path, "k1") == (b, 99.0)
+    import json
+    doc = json.load(open(path))  # the file is valid JSON
+    assert set(doc) == {"k1", "GPU A|q9|n2^20|eq0|coll0|abc"} and doc["k1"]["strip_rows"] == 4
+    with open(path, "a") as fh:  # garbage lines are ignored
+        fh.write("not json at all\n\"k2\": {\"block_threads\": \n")
+    assert lbm.lbm_tune_cache_get(path, "k2") is None
+    assert lbm.lbm_tune_cache_get(path, "k1") == (b, 99.0)
+    cfg = lbm.lbm_launch(128, 8, 4, 0)
+    assert lib.lbm_tune_cache_put(path.encode(), b'bad"key', C.byref(cfg), 1.0) == lbm.LBM_ERR_ARG
+    assert lib.lbm_tune_cache_put(str(tmp_path / "no" / "dir.json").encode(), b"k", C.byref(cfg), 1.0) == lbm.LBM_ERR_IO
+
+
+def test_autotune_option_is_validated(lib):
+    m = np.zeros((6, 9), np.uint8)
+    h = C.c_void_p()
+    o = lbm.make_options()
+    o.autotune = 2
+    assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+    assert lib.lbm_autotune(None, None, 0, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_time_steps(None, 2, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_set_launch(None, None) == lbm.LBM_ERR_ARG
