@@ -230,6 +230,49 @@ lbm_status lbm_batch_run_to_steady(lbm_batch b, double tol, int64_t max_steps, l
 lbm_status lbm_batch_permeability(lbm_batch b, double* k);
 void lbm_batch_destroy(lbm_batch b);
 
+/*
+ * x-slab of a larger domain: one domain of N_x columns cut into slabs of
+ * consecutive columns, each run by its own solver (on its own GPU or process),
+ * so that a domain larger than one GPU runs as several; the method (Sec. 2) is
+ * unchanged.  mask: the slab's columns x_offset .. x_offset + nx - 1 of the
+ * whole domain's mask (host, nx*ny*nz, x fastest), including one ghost column
+ * at each cut: bit 0 of `ghosts` says column 0 is a copy of the left
+ * neighbour's last real column, bit 1 that column nx - 1 is a copy of the right
+ * neighbour's first; a ghost is required exactly at every cut (x_offset > 0,
+ * x_offset + nx < nx_global).  drho is the whole domain's; the inlet (Zou-He,
+ * rho_out + drho) acts only on the slab holding x = 0, the outlet only on the
+ * slab holding x = nx_global - 1, and the initial density ramp runs over the
+ * whole domain.  A slab advances by pull steps (opt.in_place_pairs is
+ * ignored); its ghost columns are pulled from but never written, and no
+ * observable counts them.  After every step each cut is exchanged:
+ *   lbm_slab_export(h, side, buf): pack the real column next to the cut
+ *     (side 0: first real column, 1: last real column) -- the planes whose
+ *     direction crosses the cut towards the neighbour (c_x = -1 leftwards,
+ *     +1 rightwards; 3 of 9 in D2Q9, 5 of 19 in D3Q19), dense [planes][fluid
+ *     nodes of the column in (z, y) order] -- into buf;
+ *   lbm_slab_import(h, side, buf): unpack the neighbour's buffer into the
+ *     ghost column on that side;
+ * buf is a DEVICE buffer of lbm_slab_halo_floats(h, side, incoming) floats
+ * (incoming = 0: what export packs, 1: what import unpacks; a receiver's
+ * incoming count equals its neighbour's outgoing one), owned by the caller;
+ * both calls are enqueued on the solver's stream (order them against the
+ * neighbour's stream, or share one).  lbm_slab_observables turns observables summed
+ * over all slabs (lbm_step_observe's 8 slots, slot 3 as a maximum) into the
+ * whole domain's permeability (Darcy's law with the mass flow rate, Sec. 2;
+ * nu from Eq. 1), Kn = sqrt(pi/6)(tau - 1/2)/nx_global and residual
+ * r = sqrt(sum |du|^2 / sum |u|^2); each null output is skipped.
+ * lbm_run_to_steady, lbm_permeability and lbm_save return LBM_ERR_ARG on a slab
+ * (its driver exchanges the halos and sums the observables).  Errors:
+ * LBM_ERR_ARG for inconsistent geometry or a side without a neighbour.
+ */
+lbm_status lbm_slab_create(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, double tau, double drho,
+                           int32_t x_offset, int32_t nx_global, int32_t ghosts, const lbm_options* opt,
+                           lbm_handle* out);
+lbm_status lbm_slab_halo_floats(lbm_handle h, int32_t side, int32_t incoming, int64_t* n);
+lbm_status lbm_slab_export(lbm_handle h, int32_t side, float* buf);
+lbm_status lbm_slab_import(lbm_handle h, int32_t side, const float* buf);
+lbm_status lbm_slab_observables(lbm_handle h, const double* obs_sum, double* k, double* kn, double* residual);
+
 /* Synchronises the solver's stream and frees its resources.  Device memory of
  * solvers comes from one stream-ordered pool per device; up to 8 GB of freed
  * blocks stay cached there for the next solver, the rest returns to the

@@ -95,6 +95,12 @@ struct lbm_solver {
     int gather_batch = 0;           // rows in flight per warp of the direct gather step (0: default)
     int strip_rows = 8;             // rows per strip work item
     std::vector<uint32_t> h_off, h_smask;  // segment offsets and fluid masks (host copies)
+    // x-slab solvers (lbm_slab_create): compact indices of the exchanged
+    // columns: [0] first real column, [1] last real column (packed), [2] left
+    // ghost, [3] right ghost (unpacked)
+    bool slab = false;
+    uint32_t* d_col[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t ncol[4] = {0, 0, 0, 0};
     bool forced = false;         // force-driven, every face periodic (lbm_batch_create_forced)
     bool obs_only = false;       // the last observation was taken without stepping
     float* d_gforce = nullptr;   // body acceleration per domain (force-driven solvers)
@@ -232,6 +238,7 @@ void free_solver(lbm_handle h) {
         dfree(h, h->d_vitems);
         dfree(h, h->d_face);
         dfree(h, h->d_tiles);
+        for (auto& p : h->d_col) dfree(h, p);
         dfree(h, h->d_mask);
         dfree(h, h->d_g[0]);
         dfree(h, h->d_g[1]);
@@ -701,10 +708,39 @@ lbm_status build_tiles(lbm_handle h, int tr) {
     return LBM_OK;
 }
 
+// Compact indices of a slab's exchanged columns, fluid nodes in (z, y) order.
+lbm_status build_slab_columns(lbm_handle h) {
+    const DomainDev& G = h->hdom[0];
+    const int first = (G.ghost & 1u) ? 1 : 0, last = G.nx - 1 - ((G.ghost & 2u) ? 1 : 0);
+    const int cols[4] = {first, last, 0, G.nx - 1};
+    const bool used[4] = {(G.ghost & 1u) != 0, (G.ghost & 2u) != 0, (G.ghost & 1u) != 0, (G.ghost & 2u) != 0};
+    for (int c = 0; c < 4; ++c) {
+        if (!used[c]) continue;
+        std::vector<uint32_t> idx;
+        const int xc = cols[c];
+        for (int z = 0; z < G.nz; ++z)
+            for (int y = 0; y < G.ny; ++y) {
+                const uint32_t g = G.seg_base + ((uint32_t)z * G.ny + (uint32_t)y) * (uint32_t)G.nseg + (uint32_t)(xc >> 5);
+                const uint32_t m = h->h_smask[g], bit = (uint32_t)(xc & 31);
+                if ((m >> bit) & 1u) idx.push_back(h->h_off[g] + (uint32_t)__builtin_popcount(m & ((1u << bit) - 1u)));
+            }
+        h->ncol[c] = (uint32_t)idx.size();
+        CK(h, dmalloc(h, &h->d_col[c], sizeof(uint32_t) * std::max<size_t>(idx.size(), 1)));
+        CK(h, cudaMemcpyAsync(h->d_col[c], idx.data(), sizeof(uint32_t) * idx.size(), cudaMemcpyHostToDevice, h->st));
+    }
+    CK(h, cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
 }  // namespace
 
+struct SlabInfo {
+    int32_t x0, nx_glob;
+    uint32_t ghost;
+};
+
 static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, int force_q,
-                              lbm_handle* out, const double* gforce = nullptr) {
+                              lbm_handle* out, const double* gforce = nullptr, const SlabInfo* slab = nullptr) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
     *out = nullptr;
     if (n < 1 || !descs) return fail(nullptr, LBM_ERR_ARG, "need at least one domain");
@@ -723,6 +759,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax ||
         (o.autotune != 0 && o.autotune != 1) || o.gather_batch < 0)
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
+    if (slab) o.in_place_pairs = 0;  // a slab's ghost columns are refreshed between single pull steps
     if (gforce) {
         o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
         for (int d = 0; d < n; ++d)
@@ -758,6 +795,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     h->q = q;
     h->eq = o.equilibrium;
     h->forced = gforce != nullptr;
+    h->slab = slab != nullptr;
     h->opt = o;
     if (o.stream) {
         h->st = (cudaStream_t)o.stream;
@@ -801,6 +839,9 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         G.rho0 = (float)o.rho_out;
         G.active = 1;
         G.mask_base = mb;
+        G.x0 = slab ? slab->x0 : 0;
+        G.nx_glob = slab ? slab->nx_glob : S.nx;
+        G.ghost = slab ? slab->ghost : 0u;
         mb += (uint64_t)S.nx * S.ny * S.nz;
         sb += D.nseg;
     }
@@ -890,6 +931,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     {
         lbm_status bs = build_items(h, o.strip_rows > 0 ? o.strip_rows : 8);
         if (bs == LBM_OK) bs = build_tiles(h, o.tile_rows > 0 ? o.tile_rows : 0);
+        if (bs == LBM_OK && slab) bs = build_slab_columns(h);
         if (bs != LBM_OK) {
             free_solver(h);
             *out = nullptr;
@@ -936,6 +978,79 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
             return fail(nullptr, ts, msg);
         }
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_slab_create(const uint8_t* mask, int32_t nx, int32_t ny, int32_t nz, double tau, double drho,
+                           int32_t x_offset, int32_t nx_global, int32_t ghosts, const lbm_options* opt,
+                           lbm_handle* out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (ghosts < 0 || ghosts > 3) return fail(nullptr, LBM_ERR_ARG, "ghosts must be 0..3");
+    if (x_offset < 0 || nx < 3 || nx_global < 3 || (int64_t)x_offset + nx > nx_global)
+        return fail(nullptr, LBM_ERR_ARG, "need 0 <= x_offset, x_offset + nx <= nx_global, nx >= 3");
+    // a column 0 past the global inlet is the left neighbour's column, and a
+    // last column short of the global outlet the right neighbour's
+    if (((ghosts & 1) != 0) != (x_offset > 0) || ((ghosts & 2) != 0) != ((int64_t)x_offset + nx < nx_global))
+        return fail(nullptr, LBM_ERR_ARG, "ghost columns must be exactly the cuts to neighbouring slabs");
+    const SlabInfo info{x_offset, nx_global, (uint32_t)ghosts};
+    lbm_domain_desc d{mask, nx, ny, nz, tau, drho};
+    return create_impl(1, &d, opt, nz > 1 ? 19 : 9, out, nullptr, &info);
+}
+
+static HaloPlanes halo_planes(int q, int cx) {
+    HaloPlanes P{};
+    for (int i = 0; i < q; ++i) {
+        const int c = q == 9 ? D2Q9::c(i, 0) : D3Q19::c(i, 0);
+        if (c == cx) P.plane[P.n++] = i;
+    }
+    return P;
+}
+
+lbm_status lbm_slab_halo_floats(lbm_handle h, int32_t side, int32_t incoming, int64_t* n) {
+    if (!h || !n) return fail(h, LBM_ERR_ARG, "null argument");
+    if (!h->slab) return fail(h, LBM_ERR_ARG, "not a slab solver");
+    if (side != 0 && side != 1) return fail(h, LBM_ERR_ARG, "side must be 0 (left cut) or 1 (right cut)");
+    if (!(h->hdom[0].ghost & (1u << side))) return fail(h, LBM_ERR_ARG, "no neighbouring slab on that side");
+    const int cx = incoming ? (side == 0 ? 1 : -1) : (side == 0 ? -1 : 1);
+    *n = (int64_t)halo_planes(h->q, cx).n * h->ncol[incoming ? 2 + side : side];
+    return LBM_OK;
+}
+
+static lbm_status slab_halo(lbm_handle h, int32_t side, bool pack, float* buf) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (!h->slab) return fail(h, LBM_ERR_ARG, "not a slab solver");
+    if (side != 0 && side != 1) return fail(h, LBM_ERR_ARG, "side must be 0 (left cut) or 1 (right cut)");
+    if (!(h->hdom[0].ghost & (1u << side))) return fail(h, LBM_ERR_ARG, "no neighbouring slab on that side");
+    if (!buf) return fail(h, LBM_ERR_ARG, "null buffer");
+    // the left cut carries the c_x = -1 planes leftwards and the c_x = +1 planes rightwards
+    const int cx = pack ? (side == 0 ? -1 : 1) : (side == 0 ? 1 : -1);
+    const int c = pack ? side : 2 + side;
+    CK(h, launch_halo(pack, h->d_g[h->cur], (uint32_t)h->pstride, h->d_col[c], h->ncol[c], halo_planes(h->q, cx), buf,
+                      h->st));
+    if (!pack) h->dom[0].has_obs = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_slab_export(lbm_handle h, int32_t side, float* buf) { return slab_halo(h, side, true, buf); }
+
+lbm_status lbm_slab_import(lbm_handle h, int32_t side, const float* buf) {
+    return slab_halo(h, side, false, const_cast<float*>(buf));
+}
+
+lbm_status lbm_slab_observables(lbm_handle h, const double* obs_sum, double* k, double* kn, double* residual) {
+    if (!h || !obs_sum) return fail(h, LBM_ERR_ARG, "null argument");
+    if (!h->slab) return fail(h, LBM_ERR_ARG, "not a slab solver");
+    const DomainHost& D = h->dom[0];
+    const DomainDev& G = h->hdom[0];
+    if (k) {
+        if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: permeability undefined");
+        DomainHost whole = D;  // Darcy's law over the whole domain: only N_y N_z and drho enter
+        whole.nx = G.nx_glob;
+        *k = darcy_k(whole, obs_sum[0], false, h->opt.rho_out);
+    }
+    if (kn) *kn = knudsen(D.tau, G.nx_glob);
+    if (residual) *residual = obs_sum[2] > 0.0 ? std::sqrt(obs_sum[1] / obs_sum[2]) : (obs_sum[1] == 0.0 ? 0.0 : INFINITY);
     return LBM_OK;
 }
 
@@ -1074,6 +1189,7 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {
 lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_status* status, int64_t* steps,
                              double* residual) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (h->slab) return fail(h, LBM_ERR_ARG, "a slab is stepped by a driver that exchanges its halos");
     if (!(tol > 0.0) || max_steps < 0) return fail(h, LBM_ERR_ARG, "need tol > 0 and max_steps >= 0");
     const size_t n = h->dom.size();
     for (auto& D : h->dom) {
@@ -1195,6 +1311,8 @@ void lbm_batch_destroy(lbm_batch b) { lbm_destroy(b); }
 
 lbm_status lbm_permeability(lbm_handle h, double* k, double* kn) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+    if (h->slab) return fail(h, LBM_ERR_ARG, "a slab's permeability needs the observables of every slab "
+                                             "(lbm_slab_observables)");
     if (!k) return fail(h, LBM_ERR_ARG, "k is null");
     bool need = false;
     for (auto& D : h->dom) need |= !D.has_obs;
@@ -1337,7 +1455,7 @@ lbm_status lbm_nn_targets(lbm_handle h, int32_t d, float* out_dev) {
     lbm_status s = check_domain(h, d);
     if (s != LBM_OK) return s;
     if (!out_dev) return fail(h, LBM_ERR_ARG, "null output");
-    if (h->forced) return fail(h, LBM_ERR_ARG, "targets are defined for pressure-driven domains");
+    if (h->forced || h->slab) return fail(h, LBM_ERR_ARG, "targets are defined for whole pressure-driven domains");
     if (h->q != 9) return fail(h, LBM_ERR_ARG, "warm-start targets are defined for 2D (D2Q9) domains");
     const DomainHost& D = h->dom[d];
     if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: targets undefined");
@@ -1350,7 +1468,8 @@ lbm_status lbm_warm_start(lbm_handle h, int32_t d, const void* pred_dev, int32_t
     lbm_status s = check_domain(h, d);
     if (s != LBM_OK) return s;
     if (!pred_dev || ld < 3) return fail(h, LBM_ERR_ARG, "need a prediction with at least 3 channels");
-    if (h->forced) return fail(h, LBM_ERR_ARG, "the warm start is defined for pressure-driven domains");
+    if (h->forced || h->slab)
+        return fail(h, LBM_ERR_ARG, "the warm start is defined for whole pressure-driven domains");
     if (h->q != 9) return fail(h, LBM_ERR_ARG, "the warm start is defined for 2D (D2Q9) domains");
     DomainHost& D = h->dom[d];
     if (D.drho == 0.0) return fail(h, LBM_ERR_ARG, "drho = 0: nothing to predict");
@@ -1373,7 +1492,7 @@ static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
 
 lbm_status lbm_save(lbm_handle h, const char* path) {
     if (!h || !path) return fail(h, LBM_ERR_ARG, "null argument");
-    if (h->forced) return fail(h, LBM_ERR_ARG, "checkpoints hold pressure-driven solvers only");
+    if (h->forced || h->slab) return fail(h, LBM_ERR_ARG, "checkpoints hold whole pressure-driven domains only");
     CK(h, cudaStreamSynchronize(h->st));
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(h, LBM_ERR_IO, std::string("cannot open ") + path);

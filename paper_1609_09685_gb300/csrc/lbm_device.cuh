@@ -76,8 +76,15 @@ struct alignas(16) DomainDev {
     uint32_t nitems;     // strip work items of the domain
     uint32_t fluid_begin;  // compact index of the domain's first fluid node (a multiple of 32)
     uint32_t fluid_end;    // one past its last fluid node
+    // x-slab of a larger domain (lbm_slab_create); plain domains: x0 = 0,
+    // nx_glob = nx, ghost = 0.  A ghost column (bit 0: x = 0, bit 1:
+    // x = nx - 1) holds the neighbouring slab's populations: it is pulled
+    // from but never written and never observed.
+    int32_t x0;       // global x of column 0
+    int32_t nx_glob;  // global N_x (the initial density ramp and Kn use it)
+    uint32_t ghost;
 };
-static_assert(sizeof(DomainDev) == 80, "DomainDev is 80 bytes");
+static_assert(sizeof(DomainDev) == 96, "DomainDev is 96 bytes");
 
 // Neighbour window of one segment, read by the stream-collide kernel:
 //   x = lo | hi << 32 holds 34 fluid bits, bit k <-> node x = 32 s - 1 + k

@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
     const int ny = D.ny;
     const bool zlo = (z == 0), zhi = (z == D.nz - 1);
     const bool xin = (x == 0), xout = (x == D.nx - 1);
+    // a slab's ghost columns are pulled from, never written or observed
+    const bool ghost = ((D.ghost & 1u) && xin) || ((D.ghost & 2u) && xout);
     const bool edge = (it.w == 0) || ((int)it.w == D.nseg - 1);
     // omega-scaled weights by |c|^2 class (0 rest, 1 axis, 2 diagonal), and 3x
     // the omega_m-scaled ones (the odd part's rate; omega_m = omega for BGK)
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             float f[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = sf[i * 32];
-            const bool fl = flq[st];
+            const bool fl = flq[st] && !ghost;
             const uint32_t kk = kdq[st];
             if (edge) {  // warp-uniform: only the first and last segment columns hold x faces
                 float g[Q];
@@ -341,11 +343,12 @@ __global__ void __launch_bounds__(256)
     if (gseg >= G.nseg_total) return;
     const DomainDev D = G.dom[__ldg(G.seg_dom + gseg)];
     const uint32_t mc = __ldg(G.seg_mask + gseg);
-    const bool fluid = (mc >> lane) & 1u;
+    const SegLoc P = locate(D, gseg, lane);
+    const bool ghost = ((D.ghost & 1u) && P.x == 0) || ((D.ghost & 2u) && P.x == D.nx - 1);
+    const bool fluid = ((mc >> lane) & 1u) && !ghost;
     const size_t PS = G.pstride;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0, v5 = 0.0, v6 = 0.0;
     if (fluid) {
-        const SegLoc P = locate(D, gseg, lane);
         const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
         float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, link = 0.f;
 #pragma unroll
@@ -432,7 +435,8 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x < kNumObs) obs[(size_t)d * kNumObs + threadIdx.x] = threadIdx.x < K ? sh[threadIdx.x][0] : 0.0;
 }
 
-// Rest equilibrium with a linear density ramp: drho(x) = drho_in (N_x-1-x)/(N_x-1).
+// Rest equilibrium with a linear density ramp: drho(x) = drho_in (N_x-1-x)/(N_x-1)
+// (global x and N_x for a slab).
 template <class L>
 __global__ void __launch_bounds__(256) k_init(Geometry G, float* __restrict__ g, float* __restrict__ uprev) {
     const int lane = threadIdx.x & 31;
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(256) k_init(Geometry G, float* __restrict__ g,
     if (!((mc >> lane) & 1u)) return;
     const SegLoc P = locate(D, gseg, lane);
     const uint32_t kd = __ldg(G.seg_off + gseg) + __popc(mc & ((1u << lane) - 1u));
-    const float dr = D.drho_in * (float)(D.nx - 1 - P.x) / (float)(D.nx - 1);
+    const float dr = D.drho_in * (float)(D.nx_glob - 1 - D.x0 - P.x) / (float)(D.nx_glob - 1);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) g[(size_t)i * G.pstride + kd] = (float)L::wd(i) * dr;
     for (int a = 0; a < L::D; ++a) uprev[(size_t)a * G.pstride + kd] = 0.f;

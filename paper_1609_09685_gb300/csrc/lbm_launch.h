@@ -90,6 +90,16 @@ cudaError_t launch_pore_d2(const uint8_t* mask, int nx, int ny, int nz, uint32_t
 cudaError_t launch_local_kn(const uint8_t* mask, const uint32_t* d2, uint64_t total, double tau, double* h_out,
                             double* kn_out, cudaStream_t st);
 
+// Halo transfer of a slab (slab.cu): the planes a cut exchanges, packed from
+// (pack) or unpacked into (!pack) the column whose fluid nodes' compact
+// indices are idx[0..n), buf dense [P.n][n].
+struct HaloPlanes {
+    int n;
+    int plane[5];
+};
+cudaError_t launch_halo(bool pack, float* g, uint32_t PS, const uint32_t* idx, uint32_t n, const HaloPlanes& P,
+                        float* buf, cudaStream_t st);
+
 // Record the detail string lbm_last_error(NULL) returns on this thread (capi.cu).
 void set_thread_error(const std::string& msg);
 

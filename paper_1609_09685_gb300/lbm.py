@@ -134,6 +134,11 @@ def load(path: Optional[str] = None):
         "lbm_batch_permeability": (i32, [P, P]),
         "lbm_batch_destroy": (None, [P]),
         "lbm_lattice": (i32, [i32, P, P, P, P, P]),
+        "lbm_slab_create": (i32, [P, i32, i32, i32, d, d, i32, i32, i32, P, P]),
+        "lbm_slab_halo_floats": (i32, [P, i32, i32, P]),
+        "lbm_slab_export": (i32, [P, i32, P]),
+        "lbm_slab_import": (i32, [P, i32, P]),
+        "lbm_slab_observables": (i32, [P, P, P, P, P]),
         "lbm_get_launch": (i32, [P, P]),
         "lbm_set_launch": (i32, [P, P]),
         "lbm_time_steps": (i32, [P, i32, P]),
@@ -473,6 +478,44 @@ def lbm_lattice(q: int):
     fz = np.zeros(q, np.int32)
     _check(load().lbm_lattice(int(q), _ptr(c), _ptr(w), _ptr(o), _ptr(fy), _ptr(fz)))
     return c, w, o, fy, fz
+
+
+def lbm_slab_create(mask, tau: float, drho: float, x_offset: int, nx_global: int, ghosts: int,
+                    options: Optional[lbm_options] = None) -> Solver:
+    """One x-slab (ghost columns included in `mask`) of a domain of nx_global columns."""
+    m = _mask(mask)
+    o = options or make_options()
+    h = C.c_void_p()
+    nz, ny, nx = (1,) + m.shape if m.ndim == 2 else m.shape
+    _check(load().lbm_slab_create(_ptr(m), nx, ny, nz, tau, drho, int(x_offset), int(nx_global), int(ghosts),
+                                  C.byref(o), C.byref(h)))
+    return Solver(h, [m], [tau], [drho], o)
+
+
+def lbm_slab_halo_floats(s: Solver, side: int, incoming: bool = False) -> int:
+    n = C.c_int64()
+    _check(load().lbm_slab_halo_floats(s.handle, int(side), 1 if incoming else 0, C.byref(n)), s.handle)
+    return n.value
+
+
+def lbm_slab_export(s: Solver, side: int, buf) -> None:
+    """Pack the real column next to cut `side` into the device buffer `buf`
+    (a pointer, or an object with data_ptr())."""
+    _check(load().lbm_slab_export(s.handle, int(side), _dp(buf)), s.handle)
+
+
+def lbm_slab_import(s: Solver, side: int, buf) -> None:
+    _check(load().lbm_slab_import(s.handle, int(side), _dp(buf)), s.handle)
+
+
+def lbm_slab_observables(s: Solver, obs_sum) -> tuple:
+    """(k, Kn, residual) of the whole domain from observables summed over its slabs."""
+    o = np.ascontiguousarray(obs_sum, np.float64).reshape(-1)
+    if o.size < NUM_OBS:
+        raise ValueError("need the 8 observables")
+    k, kn, r = C.c_double(), C.c_double(), C.c_double()
+    _check(load().lbm_slab_observables(s.handle, _ptr(o), C.byref(k), C.byref(kn), C.byref(r)), s.handle)
+    return k.value, kn.value, r.value
 
 
 def lbm_get_launch(s: Solver) -> dict:
