@@ -99,6 +99,14 @@ typedef struct lbm_options {
     int32_t autotune;        /* 1: run lbm_autotune at creation (with tune_cache); 0 (default): keep the launch
                                 configuration given by the fields above, i.e. force the defaults */
     const char* tune_cache;  /* JSON cache file of lbm_autotune (NULL: none); read and updated */
+    /* Device memory of the solver's buffers: NULL, NULL (default) = the library's stream-ordered pool;
+       otherwise every buffer comes from alloc_fn(alloc_ctx, bytes, stream) -- NULL return = out of memory,
+       the call then fails with LBM_ERR_OOM after returning what it had -- and goes back through
+       free_fn(alloc_ctx, ptr, stream).  Both or neither.  (How a framework such as PyTorch lends its
+       caching allocator to the solver.) */
+    void* (*alloc_fn)(void* ctx, size_t bytes, void* stream);
+    void (*free_fn)(void* ctx, void* ptr, void* stream);
+    void* alloc_ctx;
 } lbm_options;
 
 /* One domain of a batch. */
@@ -341,6 +349,22 @@ lbm_status lbm_tune_key_for(const char* device_name, int32_t q, int64_t fluid_no
 lbm_status lbm_tune_cache_get(const char* path, const char* key, lbm_launch* cfg, double* us_per_step,
                               int32_t* found);
 lbm_status lbm_tune_cache_put(const char* path, const char* key, const lbm_launch* cfg, double us_per_step);
+
+/*
+ * Checked build (compiled with -DLBM_CHECKED; the paper has no counterpart:
+ * a failure-detection aid).  Its pull and direct gather steps compare every
+ * population index they take from the neighbour-window table with the
+ * buffer's extent; an index outside is not used and sets a device error bit
+ * that the next observation (lbm_step_observe, lbm_run_to_steady,
+ * lbm_permeability, lbm_profile_steps) returns as LBM_ERR_INTERNAL, so a
+ * corrupted table never turns into a bad memory access.
+ * lbm_build_checked: *checked = 1 in such a build, else 0.
+ * lbm_debug_corrupt_window: overwrite the compact base index of segment seg's
+ * window record with value (synchronises the solver's stream) -- a fault
+ * injection for testing the checks; LBM_ERR_ARG in a regular build.
+ */
+lbm_status lbm_build_checked(int32_t* checked);
+lbm_status lbm_debug_corrupt_window(lbm_handle h, uint32_t seg, uint32_t value);
 
 /* Number of domains, lattice size Q, and fluid node count of domain d. */
 lbm_status lbm_info(lbm_handle h, int32_t* n_domains, int32_t* q, int64_t* fluid_nodes_total);

@@ -180,14 +180,15 @@ __device__ __forceinline__ void aa_gather_body(const HotArgs& A) {
             src_elems<L>(e[j], w, PS, win_idx<0>(w[C]), y == 0, y == ny - 1, zlo, zhi,
                          std::make_integer_sequence<int, Q>{});
 #pragma unroll
-            for (int i = 0; i < Q; ++i) f[j][i] = g[e[j][i]];
+            for (int i = 0; i < Q; ++i) f[j][i] = g[chk_load(e[j][i], (uint32_t)Q * PS, A.err)];
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega, D.omega_m);
             if (fl[j]) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) g[e[j][opp<L>(i)]] = f[j][i];
+                for (int i = 0; i < Q; ++i)
+                    if (chk_store(e[j][opp<L>(i)], (uint32_t)Q * PS, A.err)) g[e[j][opp<L>(i)]] = f[j][i];
             }
         }
     }
@@ -292,7 +293,7 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
                          std::make_integer_sequence<int, Q>{});
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                f[j][i] = g[e[i]];
+                f[j][i] = g[chk_load(e[i], (uint32_t)Q * PS, A.err)];
                 we[(j * Q + i) * 32] = e[i];
             }
         }
@@ -301,7 +302,10 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
             relax<L, EQ>(f[j], edge, xin, xout, D.drho_in, D.rho0, D.omega, D.omega_m);
             if ((flb >> j) & 1u) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) g[we[(j * Q + opp<L>(i)) * 32]] = f[j][i];
+                for (int i = 0; i < Q; ++i) {
+                    const uint32_t e = we[(j * Q + opp<L>(i)) * 32];
+                    if (chk_store(e, (uint32_t)Q * PS, A.err)) g[e] = f[j][i];
+                }
             }
         }
     }

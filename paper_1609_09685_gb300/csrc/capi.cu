@@ -19,11 +19,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
 using namespace lbmgb;
+
+namespace {
+// NVTX range for the lifetime of a scope (named ranges in Nsight timelines;
+// header-only, no cost without a tool attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -210,6 +223,12 @@ cudaError_t solver_pool(cudaMemPool_t* pool) {
 
 template <class T>
 cudaError_t dmalloc(lbm_handle h, T** ptr, size_t bytes) {
+    if (h->opt.alloc_fn) {  // the caller's allocator
+        void* p = h->opt.alloc_fn(h->opt.alloc_ctx, bytes, h->st);
+        if (!p) return cudaErrorMemoryAllocation;
+        *ptr = static_cast<T*>(p);
+        return cudaSuccess;
+    }
     cudaMemPool_t pool = nullptr;
     cudaError_t e = solver_pool(&pool);
     if (e != cudaSuccess) return e;
@@ -218,7 +237,10 @@ cudaError_t dmalloc(lbm_handle h, T** ptr, size_t bytes) {
 
 template <class T>
 void dfree(lbm_handle h, T*& p) {
-    if (p) cudaFreeAsync(p, h->st);
+    if (p) {
+        if (h->opt.free_fn) h->opt.free_fn(h->opt.alloc_ctx, (void*)p, h->st);
+        else cudaFreeAsync(p, h->st);
+    }
     p = nullptr;
 }
 
@@ -398,10 +420,10 @@ lbm_status run_steps(lbm_handle h, int64_t n, bool obs) {
 
 lbm_status device_error(lbm_handle h, uint32_t word) {
     if (word == 0) return LBM_OK;
-    char buf[160];
-    std::snprintf(buf, sizeof(buf),
-                  "device error word 0x%x: a staged gather copy did not complete within its wait limit", word);
-    return fail(h, LBM_ERR_INTERNAL, buf);
+    std::string m = "device error word " + std::to_string(word) + ":";
+    if (word & 1u) m += " a staged gather copy did not complete within its wait limit;";
+    if (word & 2u) m += " a population index from the index tables was out of range (access skipped);";
+    return fail(h, LBM_ERR_INTERNAL, m);
 }
 
 lbm_status store_obs(lbm_handle h) {
@@ -569,6 +591,7 @@ void lbm_options_default(lbm_options* o) {
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
                     double d_face, void* stream, uint8_t* mask_out, int32_t* iterations) {
+    Range r("lbm_qsgs");
     if (!mask_out) return fail(nullptr, LBM_ERR_ARG, "mask_out is null");
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "sizes must be >= 1");
     const uint64_t N = (uint64_t)nx * ny * nz;
@@ -580,11 +603,17 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
     QsgsScratch sc{};
     uint8_t* d_mask = nullptr;
     lbm_status rs = LBM_OK;
-    cudaError_t e = cudaMalloc(&sc.keys, sizeof(uint64_t) * N);
-    if (e == cudaSuccess) e = cudaMalloc(&sc.start, N);
-    if (e == cudaSuccess) e = cudaMalloc(&sc.counter, sizeof(unsigned long long));
+    // scratch from the solvers' stream-ordered pool, on the caller's stream
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = solver_pool(&pool);
+    auto palloc = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, pool, st);
+    };
+    palloc(&sc.keys, sizeof(uint64_t) * N);
+    palloc(&sc.start, N);
+    palloc(&sc.counter, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&sc.host_counter, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&d_mask, N);
+    palloc(&d_mask, N);
     if (e != cudaSuccess) {
         rs = cuda_fail(nullptr, e, "qsgs allocation");
     } else {
@@ -602,11 +631,10 @@ lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double co
             if (iterations) *iterations = it;
         }
     }
-    cudaFree(sc.keys);
-    cudaFree(sc.start);
-    cudaFree(sc.counter);
+    for (void* p : {(void*)sc.keys, (void*)sc.start, (void*)sc.counter, (void*)d_mask})
+        if (p) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);  // the pinned counter may be read by work still queued on an error path
     if (sc.host_counter) cudaFreeHost(sc.host_counter);
-    cudaFree(d_mask);
     return rs;
 }
 
@@ -757,7 +785,7 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         (o.in_place_pairs != 0 && o.in_place_pairs != 1) ||
         (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
         !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax ||
-        (o.autotune != 0 && o.autotune != 1) || o.gather_batch < 0)
+        (o.autotune != 0 && o.autotune != 1) || o.gather_batch < 0 || (!o.alloc_fn != !o.free_fn))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (slab) o.in_place_pairs = 0;  // a slab's ghost columns are refreshed between single pull steps
     if (gforce) {
@@ -1055,6 +1083,7 @@ lbm_status lbm_slab_observables(lbm_handle h, const double* obs_sum, double* k, 
 }
 
 lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_options* opt, lbm_handle* out) {
+    Range r("lbm_batch_create");
     return create_impl(n, descs, opt, 0, out);
 }
 
@@ -1098,6 +1127,7 @@ lbm_status lbm_domain_fluid_nodes(lbm_handle h, int32_t d, int64_t* fluid_nodes)
 }
 
 lbm_status lbm_step(lbm_handle h, int64_t nsteps) {
+    Range r("lbm_step");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return LBM_OK;
@@ -1120,9 +1150,9 @@ lbm_status lbm_local_knudsen(lbm_handle h, int32_t d, uint32_t* d2_out, double* 
     uint32_t *d2 = nullptr, *tmp = nullptr;
     double* dev = nullptr;  // h then kn, total doubles each
     auto release = [&]() {
-        if (d2) cudaFreeAsync(d2, h->st);
-        if (tmp) cudaFreeAsync(tmp, h->st);
-        if (dev) cudaFreeAsync(dev, h->st);
+        dfree(h, d2);
+        dfree(h, tmp);
+        dfree(h, dev);
     };
     cudaError_t e = dmalloc(h, &d2, sizeof(uint32_t) * total);
     if (e == cudaSuccess) e = dmalloc(h, &tmp, sizeof(uint32_t) * total);
@@ -1174,6 +1204,7 @@ lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int
 }
 
 lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {
+    Range r("lbm_step_observe");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps < 0");
     lbm_status s = run_steps(h, nsteps, true);
@@ -1188,6 +1219,7 @@ lbm_status lbm_step_observe(lbm_handle h, int64_t nsteps, double* obs) {
 
 lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_status* status, int64_t* steps,
                              double* residual) {
+    Range rr("lbm_run_to_steady");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (h->slab) return fail(h, LBM_ERR_ARG, "a slab is stepped by a driver that exchanges its halos");
     if (!(tol > 0.0) || max_steps < 0) return fail(h, LBM_ERR_ARG, "need tol > 0 and max_steps >= 0");
@@ -1220,6 +1252,7 @@ lbm_status lbm_run_to_steady(lbm_handle h, double tol, int64_t max_steps, lbm_st
             break;
         }
         const int64_t k = std::min<int64_t>(N, max_steps - taken);
+        Range ri("check interval");
         s = run_steps(h, k, true);
         if (s != LBM_OK) return s;
         CK(h, cudaStreamSynchronize(h->st));
@@ -1345,7 +1378,7 @@ lbm_status lbm_get_fields(lbm_handle h, int32_t d, double* rho, double* ux, doub
     const DomainHost& D = h->dom[d];
     const size_t N = (size_t)D.nx * D.ny * D.nz;
     double* buf = nullptr;
-    CK(h, cudaMalloc(&buf, sizeof(double) * N * 4));
+    CK(h, dmalloc(h, &buf, sizeof(double) * N * 4));
     const cudaError_t e1 = launch_export_fields(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out,
                                                 h->d_g[h->cur], buf, buf + N, buf + 2 * N,
                                                 h->q == 19 ? buf + 3 * N : nullptr, h->st);
@@ -1356,7 +1389,7 @@ lbm_status lbm_get_fields(lbm_handle h, int32_t d, double* rho, double* ux, doub
     if (e == cudaSuccess && h->q == 19)
         e = cudaMemcpyAsync(uz, buf + 3 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    cudaFree(buf);
+    dfree(h, buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_fields");
     if (h->q == 9 && uz) std::memset(uz, 0, sizeof(double) * N);
     return LBM_OK;
@@ -1369,12 +1402,12 @@ lbm_status lbm_get_populations(lbm_handle h, int32_t d, double* f) {
     const DomainHost& D = h->dom[d];
     const size_t M = (size_t)D.nx * D.ny * D.nz * h->q;
     double* buf = nullptr;
-    CK(h, cudaMalloc(&buf, sizeof(double) * M));
+    CK(h, dmalloc(h, &buf, sizeof(double) * M));
     cudaError_t e = launch_export_pops(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out, h->d_g[h->cur],
                                        buf, h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, buf, sizeof(double) * M, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    cudaFree(buf);
+    dfree(h, buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_populations");
     return LBM_OK;
 }
@@ -1386,12 +1419,12 @@ lbm_status lbm_set_populations(lbm_handle h, int32_t d, const double* f) {
     const DomainHost& D = h->dom[d];
     const size_t M = (size_t)D.nx * D.ny * D.nz * h->q;
     double* buf = nullptr;
-    CK(h, cudaMalloc(&buf, sizeof(double) * M));
+    CK(h, dmalloc(h, &buf, sizeof(double) * M));
     cudaError_t e = cudaMemcpyAsync(buf, f, sizeof(double) * M, cudaMemcpyHostToDevice, h->st);
     if (e == cudaSuccess)
         e = launch_import_pops(h->q, h->geom(), D.seg_begin, D.nseg, h->opt.rho_out, buf, h->d_g[h->cur], h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    cudaFree(buf);
+    dfree(h, buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_populations");
     h->dom[d].has_obs = false;
     h->dom[d].forced_state = false;
@@ -1409,7 +1442,7 @@ lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const floa
     const float *a = drho, *b = ux, *c = uy, *z = (h->q == 19) ? uz : nullptr;
     cudaError_t e = cudaSuccess;
     if (!on_device) {
-        CK(h, cudaMalloc(&buf, sizeof(float) * N * 4));
+        CK(h, dmalloc(h, &buf, sizeof(float) * N * 4));
         e = cudaMemcpyAsync(buf, drho, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(buf + N, ux, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 2 * N, uy, sizeof(float) * N, cudaMemcpyHostToDevice, h->st);
@@ -1424,7 +1457,7 @@ lbm_status lbm_set_fields(lbm_handle h, int32_t d, const float* drho, const floa
         e = launch_set_fields(h->q, h->eq, h->geom(), D.seg_begin, D.nseg, a, b, c, z, h->d_g[h->cur],
                               h->d_uprev, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    cudaFree(buf);
+    dfree(h, buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
     h->dom[d].has_obs = false;
     h->dom[d].forced_state = false;
@@ -1821,7 +1854,7 @@ lbm_status lbm_time_steps(lbm_handle h, int32_t nsteps, double* us_per_step) {
     // restore the state (an even number of steps leaves the current buffer in place)
     h->cur = cur0;
     cudaError_t e2 = cudaMemcpyAsync(h->d_g[cur0], save, bytes, cudaMemcpyDeviceToDevice, h->st);
-    cudaFreeAsync(save, h->st);
+    dfree(h, save);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(h->st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1874,6 +1907,7 @@ lbm_status lbm_tune_cache_put(const char* path, const char* key, const lbm_launc
 }
 
 lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lbm_tune_result* out) {
+    Range rg("lbm_autotune");
     if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
     if (nsteps < 0 || nsteps > 10000) return fail(h, LBM_ERR_ARG, "nsteps must be in [0, 10000]");
     const int steps = nsteps == 0 ? 20 : (nsteps + 1) / 2 * 2;
@@ -1935,6 +1969,31 @@ lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lb
         if (s != LBM_OK) return fail(h, s, lbm_last_error(nullptr));
     }
     if (out) *out = r;
+    return LBM_OK;
+}
+
+
+lbm_status lbm_debug_corrupt_window(lbm_handle h, uint32_t seg, uint32_t value) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "null handle");
+#ifdef LBM_CHECKED
+    if (seg >= h->nseg_total) return fail(h, LBM_ERR_ARG, "segment out of range");
+    CK(h, cudaStreamSynchronize(h->st));
+    CK(h, cudaMemcpy(reinterpret_cast<uint32_t*>(h->d_win + seg) + 2, &value, sizeof(value), cudaMemcpyHostToDevice));
+    return LBM_OK;
+#else
+    (void)seg;
+    (void)value;
+    return fail(h, LBM_ERR_ARG, "only a checked build (LBM_CHECKED) accepts a corrupted index table");
+#endif
+}
+
+lbm_status lbm_build_checked(int32_t* checked) {
+    if (!checked) return fail(nullptr, LBM_ERR_ARG, "null argument");
+#ifdef LBM_CHECKED
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
     return LBM_OK;
 }
 

@@ -167,11 +167,12 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             kdq[st] = win_idx<0>(w[C]);
             sfq[st] = OBS ? src_fluid_mask<L>(w, std::make_integer_sequence<int, Q>{}) : 0u;
             const uint32_t sbase = sb0 + 4u * (uint32_t)(st * SL * 32);
-            issue_row<L>(A.src[0], PS, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase,
+            issue_row<L>(A.src[0], PS, w, kdq[st], y == 0, y == ny - 1, zlo, zhi, sbase, A.err,
                          std::make_integer_sequence<int, Q>{});
             if (OBS) {
 #pragma unroll
-                for (int a = 0; a < L::D; ++a) cp_async4(sbase + 4u * (32u * (Q + a)), uprev + (size_t)a * PS + kdq[st]);
+                for (int a = 0; a < L::D; ++a)
+                    cp_async4(sbase + 4u * (32u * (Q + a)), uprev + (size_t)a * PS + chk_load(kdq[st], PS, A.err));
             }
             if (kSlide && next + 1 < nrows) {
 #pragma unroll
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(256, MinBlocks<L>::value)
             float f[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = sf[i * 32];
-            const bool fl = flq[st] && !ghost;
+            const bool fl = flq[st] && !ghost && chk_store(kdq[st], PS, A.err);
             const uint32_t kk = kdq[st];
             if (edge) {  // warp-uniform: only the first and last segment columns hold x faces
                 float g[Q];

@@ -8,9 +8,39 @@
 
 #include "lbm_device.cuh"
 
+// Checked build (-DLBM_CHECKED): every population index the step kernels take
+// from the index tables (windows) is compared with the extent of the buffer it
+// addresses.  An index outside is not used -- a load reads element 0 instead,
+// a store is skipped -- and bit 1 of the device error word is set, which the
+// next observation reports as LBM_ERR_INTERNAL.  The regular build compiles
+// the checks away.
 namespace lbmgb {
 
 namespace {
+
+__device__ __forceinline__ uint32_t chk_load(uint32_t e, uint32_t lim, uint32_t* err) {
+#ifdef LBM_CHECKED
+    if (e < lim) return e;
+    atomicOr(err, 2u);
+    return 0u;
+#else
+    (void)lim;
+    (void)err;
+    return e;
+#endif
+}
+__device__ __forceinline__ bool chk_store(uint32_t e, uint32_t lim, uint32_t* err) {
+#ifdef LBM_CHECKED
+    if (e < lim) return true;
+    atomicOr(err, 2u);
+    return false;
+#else
+    (void)e;
+    (void)lim;
+    (void)err;
+    return true;
+#endif
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -263,10 +293,13 @@ __device__ __forceinline__ void cp_async_wait() {
 template <class L, int... Is>
 __device__ __forceinline__ void issue_row(const float* __restrict__ src, uint32_t PS, const Win (&w)[L::NROW],
                                           uint32_t kd, bool ylo, bool yhi, bool zlo, bool zhi, uint32_t sbase,
-                                          std::integer_sequence<int, Is...>) {
+                                          uint32_t* err, std::integer_sequence<int, Is...>) {
     // a direction with c_y = +1 pulls from row y - 1, mirrored when y = 0, etc.
+    (void)err;
     (cp_async4(sbase + 4u * (32u * Is),
-               src + src_elem<L, Is>(w, PS, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, Dir<Is, L>::cz > 0 ? zlo : zhi)),
+               src + chk_load(src_elem<L, Is>(w, PS, kd, Dir<Is, L>::cy > 0 ? ylo : yhi,
+                                                  Dir<Is, L>::cz > 0 ? zlo : zhi),
+                                  (uint32_t)L::Q * PS, err)),
      ...);
 }
 

@@ -65,7 +65,41 @@ class lbm_options(C.Structure):
         ("gather_batch", C.c_int32),
         ("autotune", C.c_int32),
         ("tune_cache", C.c_char_p),
+        ("alloc_fn", C.c_void_p),
+        ("free_fn", C.c_void_p),
+        ("alloc_ctx", C.c_void_p),
     ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+def torch_allocator(fail_after: Optional[int] = None, log: Optional[list] = None):
+    """(alloc_fn, free_fn) callbacks that lend PyTorch's CUDA caching allocator
+    to a solver (pass them to make_options).  fail_after: the allocation with
+    that index (0-based) and every later one return NULL -- an injected
+    out-of-memory for tests.  log: receives ("alloc", ptr, bytes) and
+    ("free", ptr) events."""
+    import torch
+    count = [0]
+
+    def _alloc(ctx, nbytes, stream):
+        i = count[0]
+        count[0] += 1
+        if fail_after is not None and i >= fail_after:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        if log is not None:
+            log.append(("alloc", int(p), int(nbytes)))
+        return int(p)
+
+    def _free(ctx, ptr, stream):
+        if log is not None:
+            log.append(("free", int(ptr)))
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 class lbm_launch(C.Structure):
@@ -100,9 +134,11 @@ def library_path() -> str:
 
 
 def load(path: Optional[str] = None):
-    """Load the CUDA library (raises if it has not been built)."""
+    """Load the CUDA library (raises if it has not been built).  A path loads
+    that build instead (for instance the checked one) and makes it the
+    library every function of this module calls, until `unload()`."""
     global _lib
-    if _lib is not None:
+    if _lib is not None and path is None:
         return _lib
     p = path or _build.LIB
     if not os.path.exists(p):
@@ -139,6 +175,8 @@ def load(path: Optional[str] = None):
         "lbm_slab_export": (i32, [P, i32, P]),
         "lbm_slab_import": (i32, [P, i32, P]),
         "lbm_slab_observables": (i32, [P, P, P, P, P]),
+        "lbm_build_checked": (i32, [P]),
+        "lbm_debug_corrupt_window": (i32, [P, C.c_uint32, C.c_uint32]),
         "lbm_get_launch": (i32, [P, P]),
         "lbm_set_launch": (i32, [P, P]),
         "lbm_time_steps": (i32, [P, i32, P]),
@@ -181,6 +219,12 @@ def load(path: Optional[str] = None):
     return lib
 
 
+def unload() -> None:
+    """Forget the loaded library handle (the next call loads the default build)."""
+    global _lib
+    _lib = None
+
+
 def _check(st: int, handle=None, soft=_SOFT) -> int:
     if st in soft:
         return st
@@ -207,7 +251,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
                  in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0, tile_rows=0, gather_batch=0,
-                 autotune=False, tune_cache=None) -> lbm_options:
+                 autotune=False, tune_cache=None, allocator=None) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -228,6 +272,10 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.gather_batch = gather_batch
     o.autotune = 1 if autotune else 0
     o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
+    if allocator is not None:  # (alloc_fn, free_fn) callbacks, kept alive by the options object
+        o._allocator = allocator
+        o.alloc_fn = C.cast(allocator[0], C.c_void_p)
+        o.free_fn = C.cast(allocator[1], C.c_void_p)
     return o
 
 
@@ -516,6 +564,16 @@ def lbm_slab_observables(s: Solver, obs_sum) -> tuple:
     k, kn, r = C.c_double(), C.c_double(), C.c_double()
     _check(load().lbm_slab_observables(s.handle, _ptr(o), C.byref(k), C.byref(kn), C.byref(r)), s.handle)
     return k.value, kn.value, r.value
+
+
+def lbm_build_checked() -> bool:
+    c = C.c_int32()
+    _check(load().lbm_build_checked(C.byref(c)))
+    return bool(c.value)
+
+
+def lbm_debug_corrupt_window(s: Solver, seg: int, value: int) -> None:
+    _check(load().lbm_debug_corrupt_window(s.handle, int(seg), int(value)), s.handle)
 
 
 def lbm_get_launch(s: Solver) -> dict:
