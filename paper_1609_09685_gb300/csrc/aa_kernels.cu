@@ -694,12 +694,24 @@ __global__ void __launch_bounds__((kTileSegs + 1) * 32) k_aa_gather_staged(const
 // vector per plane (a warp moves 32 V contiguous slots per plane), and the
 // face bits select the Zou-He closure for inlet and outlet nodes.  Slots
 // between domains belong to no node; they hold zero, which relaxes to zero.
+#ifndef LBM_LOCAL_VEC_2D
+#define LBM_LOCAL_VEC_2D 4
+#endif
+#ifndef LBM_LOCAL_VEC_3D
+#define LBM_LOCAL_VEC_3D 2
+#endif
 template <class L>
 struct LocalVec {
-    static constexpr int value = (L::Q == 9) ? 4 : 2;
+    static constexpr int value = (L::Q == 9) ? LBM_LOCAL_VEC_2D : LBM_LOCAL_VEC_3D;
 };
 template <int V>
 struct VecT;
+template <>
+struct VecT<1> {
+    using T = float;
+    __device__ static void split(const float a, float (&o)[1]) { o[0] = a; }
+    __device__ static float join(const float (&o)[1]) { return o[0]; }
+};
 template <>
 struct VecT<4> {
     using T = float4;
