@@ -58,6 +58,10 @@ def parse():
                    help="also run the paper's force-driven periodic 3D experiment (100^3, phi 0.748587)")
     p.add_argument("--local-kn", action="store_true",
                    help="also time the local pore-size / local-Kn pass over every domain")
+    p.add_argument("--conv-bench", action="store_true",
+                   help="only time the warm-start network's convolution shapes on both tensor-core paths "
+                        "(mma.sync and tcgen05) and print that line")
+    p.add_argument("--conv-reps", type=int, default=20)
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default launch configuration instead of running the library's autotuner")
     p.add_argument("--tile-rows", type=int, default=0,
@@ -572,6 +576,52 @@ def roofline_of(lbm, wl_name, sp, stream, N, steps, warmup, coll, barrier, peak,
             "autotune": tune}
 
 
+def run_conv_bench(args):
+    """The 3x3 convolutions of the 8-level warm-start U-Net (batch 8, 256x512
+    input, channels 16, 32, 32, 64, 64, 128, 128, 128) on the mma.sync and
+    tcgen05 paths: CUDA-event time per launch and TFLOP/s (2 x 9 x Cin x Cout
+    per output pixel)."""
+    import torch
+
+    from paper_1609_09685_gb300 import build as B
+    from paper_1609_09685_gb300 import lbm
+    B.build()
+    lbm.load()
+    batch, chans = 8, (16, 32, 32, 64, 64, 128, 128, 128)
+    rows = []
+    old = lbm.lbm_nn_get_conv_impl()
+    try:
+        for lvl, c in enumerate(chans):
+            h, w = 256 >> lvl, 512 >> lvl
+            for cin in ((chans[lvl - 1] if lvl else 16), c):
+                x = torch.randn(batch, h, w, cin, device="cuda").to(torch.bfloat16)
+                wt = (torch.randn(9, c, cin, device="cuda") * 0.1).to(torch.bfloat16)
+                b = torch.zeros(c, device="cuda")
+                y = torch.empty(batch, h, w, c, device="cuda", dtype=torch.bfloat16)
+                row = {"n": batch, "h": h, "w": w, "cin": cin, "cout": c}
+                for name, impl in (("mma_sync", lbm.LBM_NN_CONV_MMA_SYNC), ("tcgen05", lbm.LBM_NN_CONV_TCGEN05)):
+                    lbm.lbm_nn_set_conv_impl(impl)
+                    for _ in range(3):
+                        lbm.lbm_nn_conv_fwd(x, batch, h, w, cin, wt, b, 9, c, 1, y)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(args.conv_reps):
+                        lbm.lbm_nn_conv_fwd(x, batch, h, w, cin, wt, b, 9, c, 1, y)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    us = e0.elapsed_time(e1) * 1e3 / args.conv_reps
+                    row[name] = {"us": us, "tflops": 2.0 * 9 * cin * c * batch * h * w / us / 1e6}
+                lbm.lbm_nn_sync_status()
+                rows.append(row)
+    finally:
+        lbm.lbm_nn_set_conv_impl(old)
+    tot = {k: sum(r[k]["us"] for r in rows) for k in ("mma_sync", "tcgen05")}
+    print(json.dumps({"metric": "warm-start U-Net 3x3 convolutions, us per forward pass (batch 8)",
+                      "value": tot, "unit": "us", "layers": rows}), flush=True)
+    return 0
+
+
 def run_native(args):
     import torch
 
@@ -743,6 +793,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.conv_bench:
+        return run_conv_bench(args)
     return run_native(args)
 
 

@@ -523,9 +523,27 @@ lbm_status lbm_load(const char* path, const lbm_options* opt, lbm_handle* out);
  * return LBM_ERR_CUDA.  Details come from lbm_last_error(NULL).
  */
 
+/* Tensor-core path of the convolutions (process-wide; all give the same
+ * result up to FP32 summation order):
+ *   LBM_NN_CONV_MMA_SYNC  warp-level mma.sync m16n8k16, operands in registers;
+ *   LBM_NN_CONV_TCGEN05   5th-generation tcgen05.mma issued by one thread per
+ *                         block, operands in shared memory, the FP32
+ *                         accumulator in tensor memory;
+ *   LBM_NN_CONV_AUTO      (default) tcgen05 for layers with cin >= 32,
+ *                         cout >= 64 and images of w >= 64 and h w >= 2048
+ *                         (where it measured faster on GB300), else mma.sync.
+ * lbm_nn_sync_status synchronises `stream` and returns LBM_ERR_INTERNAL if a
+ * tcgen05 convolution gave up one of its bounded waits since the last call
+ * (its output is then incomplete); it clears that record. */
+enum { LBM_NN_CONV_MMA_SYNC = 0, LBM_NN_CONV_TCGEN05 = 1, LBM_NN_CONV_AUTO = 2 };
+lbm_status lbm_nn_set_conv_impl(int32_t impl);
+int32_t lbm_nn_get_conv_impl(void);
+lbm_status lbm_nn_sync_status(void* stream);
+
 /* out = act(b + sum_{tap, ci} in[p + off_tap, ci] w[tap][co][ci]), act = ReLU if
- * relu != 0.  BF16 tensor-core implicit GEMM (mma.sync m16n8k16), FP32
- * accumulation.  bias and out_f32 (an FP32 copy of out) may be NULL. */
+ * relu != 0.  BF16 tensor-core implicit GEMM (the path lbm_nn_set_conv_impl
+ * selects), FP32 accumulation.  bias and out_f32 (an FP32 copy of out) may be
+ * NULL. */
 lbm_status lbm_nn_conv_fwd(const void* in, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wts,
                            const float* bias, int32_t taps, int32_t cout, int32_t relu, void* out,
                            float* out_f32, void* stream);

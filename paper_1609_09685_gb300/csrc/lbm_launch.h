@@ -100,6 +100,14 @@ struct HaloPlanes {
 cudaError_t launch_halo(bool pack, float* g, uint32_t PS, const uint32_t* idx, uint32_t n, const HaloPlanes& P,
                         float* buf, cudaStream_t st);
 
+// Warm-start network convolution on the tcgen05 tensor cores (unet_tc.cu), and
+// the device flag its bounded waits set (taken and cleared by tc_error_take).
+namespace nn {
+cudaError_t launch_conv_fwd_tc(const void* in, int N, int H, int W, int Cin, const void* w, const float* bias,
+                               int taps, int Cout, int relu, void* out, float* out_f32, cudaStream_t st);
+cudaError_t tc_error_take(unsigned int* word, cudaStream_t st);
+}  // namespace nn
+
 // Record the detail string lbm_last_error(NULL) returns on this thread (capi.cu).
 void set_thread_error(const std::string& msg);
 

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -392,6 +393,21 @@ lbm_status nn_fail(const char* m) {
     lbmgb::set_thread_error(m);
     return LBM_ERR_ARG;
 }
+lbm_status nn_fail(const std::string& m, lbm_status s) {
+    lbmgb::set_thread_error(m);
+    return s;
+}
+// which tensor-core path the convolutions take (process-wide)
+std::atomic<int> g_conv_impl{LBM_NN_CONV_AUTO};
+// The automatic choice, from the measured times of the warm-start network's
+// layers on GB300 (batch 8): tcgen05 is ahead only for wide layers on images of
+// at least 64 pixels per row and 2048 pixels; shallow full-resolution layers and
+// the small deep ones are faster with mma.sync.
+bool use_tcgen05(int h, int w, int cin, int cout) {
+    const int impl = g_conv_impl.load();
+    if (impl != LBM_NN_CONV_AUTO) return impl == LBM_NN_CONV_TCGEN05;
+    return cin >= 32 && cout >= 64 && w >= 64 && (long)h * w >= 2048;
+}
 lbm_status nn_launch_status() {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) return LBM_OK;
@@ -408,6 +424,24 @@ unsigned ew_grid(size_t n) {
 
 extern "C" {
 
+lbm_status lbm_nn_set_conv_impl(int32_t impl) {
+    if (impl != LBM_NN_CONV_MMA_SYNC && impl != LBM_NN_CONV_TCGEN05 && impl != LBM_NN_CONV_AUTO)
+        return nn_fail("unknown convolution path");
+    g_conv_impl.store(impl);
+    return LBM_OK;
+}
+
+int32_t lbm_nn_get_conv_impl(void) { return g_conv_impl.load(); }
+
+lbm_status lbm_nn_sync_status(void* stream) {
+    unsigned int word = 0;
+    const cudaError_t e = lbmgb::nn::tc_error_take(&word, (cudaStream_t)stream);
+    if (e != cudaSuccess) return nn_fail(std::string("lbm_nn_sync_status: ") + cudaGetErrorString(e), LBM_ERR_CUDA);
+    if (word) return nn_fail("a tensor-core convolution gave up waiting for its MMAs (output incomplete)",
+                             LBM_ERR_INTERNAL);
+    return LBM_OK;
+}
+
 lbm_status lbm_nn_conv_fwd(const void* in, int32_t n, int32_t h, int32_t w, int32_t cin, const void* wts,
                            const float* bias, int32_t taps, int32_t cout, int32_t relu, void* out, float* out_f32,
                            void* stream) {
@@ -416,6 +450,12 @@ lbm_status lbm_nn_conv_fwd(const void* in, int32_t n, int32_t h, int32_t w, int3
         return nn_fail("conv: need channels multiple of 16 and taps 1 or 9");
     if (!aligned16(in) || !aligned16(wts) || !aligned16(out)) return nn_fail("conv: tensors must be 16-byte aligned");
     if ((long)n * h > 65535) return nn_fail("conv: n*h must be <= 65535");
+    if (use_tcgen05(h, w, cin, cout)) {
+        const cudaError_t e = lbmgb::nn::launch_conv_fwd_tc(in, n, h, w, cin, wts, bias, taps, cout, relu, out,
+                                                            out_f32, (cudaStream_t)stream);
+        if (e != cudaSuccess) return nn_fail(std::string("conv (tcgen05) launch: ") + cudaGetErrorString(e), LBM_ERR_CUDA);
+        return LBM_OK;
+    }
     dim3 grid((w + lbmgb::nn::kBM - 1) / lbmgb::nn::kBM, n * h, (cout + lbmgb::nn::kBN - 1) / lbmgb::nn::kBN);
     lbmgb::nn::k_conv_fwd<<<grid, 128, 0, (cudaStream_t)stream>>>(
         (const bf16*)in, n, h, w, cin, (const bf16*)wts, bias, taps, cout, relu, (bf16*)out, out_f32);

@@ -191,6 +191,9 @@ def load(path: Optional[str] = None):
         "lbm_set_fields": (i32, [P, i32, P, P, P, P, i32]),
         "lbm_get_step": (i32, [P, P]),
         "lbm_get_history": (i32, [P, i32, P, P, P, P, i32, P]),
+        "lbm_nn_set_conv_impl": (i32, [i32]),
+        "lbm_nn_get_conv_impl": (i32, []),
+        "lbm_nn_sync_status": (i32, [P]),
         "lbm_nn_conv_fwd": (i32, [P, i32, i32, i32, i32, P, P, i32, i32, i32, P, P, P]),
         "lbm_nn_conv_bwd_data": (i32, [P, i32, i32, i32, i32, P, i32, i32, P, P, P]),
         "lbm_nn_conv_bwd_weight": (i32, [P, P, i32, i32, i32, i32, i32, i32, P, P, i32, P, C.c_size_t, P]),
@@ -691,6 +694,23 @@ def _dp(t):
     if t is None:
         return None
     return C.c_void_p(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))
+
+
+LBM_NN_CONV_MMA_SYNC = 0
+LBM_NN_CONV_TCGEN05 = 1
+LBM_NN_CONV_AUTO = 2
+
+
+def lbm_nn_set_conv_impl(impl: int) -> None:
+    _check(load().lbm_nn_set_conv_impl(int(impl)))
+
+
+def lbm_nn_get_conv_impl() -> int:
+    return int(load().lbm_nn_get_conv_impl())
+
+
+def lbm_nn_sync_status(stream=None) -> None:
+    _check(load().lbm_nn_sync_status(stream))
 
 
 def lbm_nn_conv_fwd(x, n, h, w, cin, wts, bias, taps, cout, relu, out, out_f32=None, stream=None):
