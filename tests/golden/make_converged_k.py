@@ -17,7 +17,7 @@ Sets (names as in the tests):
       seed 2026), master seed 2026
   C4  256x128x128 D3Q19, porosity 0.70, tau 0.52 and 0.6
 
-    python tests/golden/make_converged_k.py [--sets C1,C2,C3] [--procs N]
+    python tests/golden/make_converged_k.py [--sets C1,C2,C3] [--procs N] [--names A,B] [--maxiter M]
 
 Runs one process per job (spawned), longest first.  Results are appended as
 they finish to converged_k.partial.txt and the final files are written when
@@ -75,14 +75,18 @@ def cost(d):
     return d.cells * d.nx * (0.2 + (d.tau - 0.5)) * (19.0 / 9.0 if d.nz > 1 else 1.0)
 
 
+MAXITER = 400
+
+
 def solve(job):
     import oracle as O
     from oracle import steady
-    set_name, name, d = job
+    set_name, name, d = job[:3]
+    maxiter = job[3] if len(job) > 3 else MAXITER
     t0 = time.time()
     mask, _ = O.qsgs(d.shape, d.seed, d.core_p, d.porosity, d.d_face)
     perc = O.percolates(mask)
-    f, info = steady.steady_state(mask, d.tau, 1.0 + d.drho, 1.0)
+    f, info = steady.steady_state(mask, d.tau, 1.0 + d.drho, 1.0, maxiter=maxiter)
     k = O.permeability(mask, f, d.tau, 1.0 + d.drho, 1.0)
     fields = O.fields(mask, f)
     fl = np.flatnonzero(mask.ravel() == 0)
@@ -99,14 +103,15 @@ HEADER = """# FP64 oracle: converged Darcy permeability of the benchmark configu
 # mass flow rate by Darcy's law, nu = (tau - 1/2)/3 from Eq. 1), written by
 # tests/golden/make_converged_k.py from oracle/ only.  The steady state is the
 # fixed point of the oracle's FP64 step (oracle/steady.py); `residual` is the
-# max-norm of S(f) - f at the stored state.  Columns:
-# name nx ny nz seed porosity tau drho k residual evals percolates
+# max-norm of S(f) - f at the stored state; converged: the root finder met
+# its tolerance (4e-16).  Columns:
+# name nx ny nz seed porosity tau drho k residual evals percolates converged
 """
 
 
 def line(r):
     return (f"{r['name']} {r['nx']} {r['ny']} {r['nz']} {r['seed']} {r['porosity']!r} {r['tau']!r} {r['drho']!r} "
-            f"{r['k']!r} {r['residual']:.3e} {r['evals']} {int(r['percolates'])}")
+            f"{r['k']!r} {r['residual']:.3e} {r['evals']} {int(r['percolates'])} {int(r['converged'])}")
 
 
 def read_existing():
@@ -126,8 +131,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--sets", default="C1,C2,C3")
     ap.add_argument("--procs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
+    ap.add_argument("--names", default="", help="only these domains (comma list), e.g. to re-solve one")
+    ap.add_argument("--maxiter", type=int, default=MAXITER, help="Newton iterations of the root finder")
     a = ap.parse_args()
     todo = sorted(jobs(set(a.sets.split(","))), key=lambda j: -cost(j[2]))
+    if a.names:
+        keep = set(a.names.split(","))
+        todo = [j for j in todo if j[1] in keep]
+    todo = [j + (a.maxiter,) for j in todo]
     rows, samples = read_existing()
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as part:
