@@ -66,6 +66,10 @@ def parse():
                    help="keep the default launch configuration instead of running the library's autotuner")
     p.add_argument("--tile-rows", type=int, default=0,
                    help="gather step: rows per staged tile (1..4), -1 = direct loads, 0 = library default")
+    p.add_argument("--band-rows", type=int, default=0,
+                   help="band gather step rows per band (D2Q9; 0 = the library's default, -1 = not used)")
+    p.add_argument("--pair-block-mb", type=int, default=0,
+                   help="L2-blocked pairs, MB of populations per block (0 = the library's default, -1 = whole batch)")
     p.add_argument("--collision", choices=["bgk", "trt"], default="bgk",
                    help="BGK (the paper's model) or TRT with Lambda = 3/16")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -648,13 +652,15 @@ def run_native(args):
     taus = [d.tau for d in wl.domains]
     drhos = [d.drho for d in wl.domains]
     coll = lbm.LBM_COLL_TRT if args.collision == "trt" else lbm.LBM_COLL_BGK
-    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, tile_rows=args.tile_rows)
+    opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, tile_rows=args.tile_rows,
+                            band_rows=args.band_rows, pair_block_mb=args.pair_block_mb)
     s = lbm.lbm_batch_create(masks, taus, drhos, opts)
     fluid = s.fluid_nodes
     bytes_per_launch = 2 * 4 * q * fluid
     tune = None
-    if not args.no_autotune and args.tile_rows == 0:
+    if not args.no_autotune and args.tile_rows == 0 and args.band_rows == 0 and args.pair_block_mb == 0:
         tune = lbm.lbm_autotune(s)  # CUDA-event timing of every candidate on this solver's stream
+    lbm_launch_of_run = lbm.lbm_get_launch(s)  # the configuration the timed region runs
 
     def barrier():
         torch.cuda.synchronize()
@@ -685,7 +691,8 @@ def run_native(args):
         c = tune["chosen"]
         opts = lbm.make_options(stream=sp, check_interval=N, collision=coll, block_threads=c["block_threads"],
                                 strip_rows=c["strip_rows"], gather_batch=c["gather_batch"],
-                                tile_rows=c["tile_rows"])
+                                tile_rows=c["tile_rows"], band_rows=c["band_rows"] if c["band_rows"] else -1,
+                                pair_block_mb=c["pair_block_mb"] if c["pair_block_mb"] else -1)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -741,6 +748,7 @@ def run_native(args):
                 "workload": wl.name, "domains": len(wl.domains), "lattice": f"D2Q9" if q == 9 else "D3Q19",
                 "collision": "TRT (Lambda = 3/16)" if args.collision == "trt" else "BGK",
                 "gather_tile_rows": args.tile_rows,
+                "gather_launch": lbm_launch_of_run,
                 "nodes": total_nodes, "fluid_nodes": fluid, "check_interval": N,
                 "step": f"{N - 1} fused stream-collide steps + 1 observing step + FP64 reduction + "
                         "host readback (one convergence-check interval)",

@@ -107,6 +107,17 @@ typedef struct lbm_options {
     void* (*alloc_fn)(void* ctx, size_t bytes, void* stream);
     void (*free_fn)(void* ctx, void* ptr, void* stream);
     void* alloc_ctx;
+    int32_t band_rows;       /* gather step of the in-place pair (D2Q9): 1..64 = band gather step -- a block walks
+                                down up to this many rows of a piece of up to 512 nodes of the width, staging
+                                each row's compact range of every plane in a shared-memory ring by bulk copies
+                                (one copy per plane and row) -- ; -1 = not used; 0 = the library's default.
+                                Ignored with tile_rows > 0 (both > 0 is an error), for D3Q19 and for
+                                force-driven or slab solvers.  Bit-identical results either way. */
+    int32_t pair_block_mb;   /* in-place pairs run block by block: the gather step of block k + 1, then the local
+                                step of block k, each block about this many MB of populations, so that a block
+                                is still in L2 when its local step reads it (1..4096); -1 = whole-batch pairs;
+                                0 = the library's default.  Used with the direct gather step only.  Bit-identical
+                                results either way. */
 } lbm_options;
 
 /* One domain of a batch. */
@@ -298,11 +309,15 @@ void lbm_destroy(lbm_handle h);
  *   gather_batch   rows of loads a warp of the direct gather step keeps in
  *                  flight: 2 or 4 (D2Q9), 1 or 2 (D3Q19)
  *   tile_rows      0: direct gather step; 1..4: staged gather step (D2Q9)
+ *   band_rows      0: not used; 1..64: band gather step with up to this many
+ *                  rows per band (D2Q9; not together with tile_rows)
+ *   pair_block_mb  0: whole-batch pairs; 1..4096: L2-blocked pairs with blocks
+ *                  of about this many MB (with the direct gather step)
  * lbm_get_launch reports the solver's configuration; lbm_set_launch changes
  * it (LBM_ERR_ARG for a value outside the ranges above).
  */
 typedef struct lbm_launch {
-    int32_t block_threads, strip_rows, gather_batch, tile_rows;
+    int32_t block_threads, strip_rows, gather_batch, tile_rows, band_rows, pair_block_mb;
 } lbm_launch;
 lbm_status lbm_get_launch(lbm_handle h, lbm_launch* cfg);
 lbm_status lbm_set_launch(lbm_handle h, const lbm_launch* cfg);
@@ -316,7 +331,8 @@ lbm_status lbm_time_steps(lbm_handle h, int32_t nsteps, double* us_per_step);
  * Autotuner.  Times each candidate configuration with lbm_time_steps (nsteps
  * per candidate, 0 = 20) and keeps the fastest; the candidates are block size
  * {64, 128, 256} x strip rows {4, 8, 16} x gather batch (both compiled ones),
- * plus the staged gather step with 2 and 3 tile rows for D2Q9.  With
+ * plus, for D2Q9, the staged gather step with 2 and 3 tile rows and the band
+ * gather step with 16, 32 and 64 band rows.  With
  * cache_path (nullable), the choice is looked up first under the key of
  * lbm_tune_key and stored after a search.  Force-driven solvers have nothing
  * to tune (their steps are pull steps of their own kernel): the call only

@@ -688,6 +688,253 @@ __global__ void __launch_bounds__((kTileSegs + 1) * 32) k_aa_gather_staged(const
     (void)consumed;
 }
 
+// ---------------------------------------------------------------------------
+// Band gather step (D2Q9).  The direct gather step waits on scattered loads;
+// the staged one above moves many short ranges.  Here a block owns a band --
+// up to kBandSegs consecutive segment columns (a piece of the domain's width)
+// x up to kBandRowsMax rows -- and walks down its rows with a ring of NS rows
+// staged in shared memory.  Two facts keep the copies few and long:
+//   - in the compact (row-major) order the fluid nodes of a row piece, with
+//     the node on either side, are one contiguous range of every plane;
+//   - a node of row y reads plane j only in row y - c_jy (streaming) and in
+//     row y itself (bounce-back, the Zou-He unknowns, the specular image), so
+//     walking down, each plane needs one new row per step, and the rows just
+//     above and below the band only in the three planes that stream out of
+//     them.
+// A staged row is therefore nine bulk copies of one range each (three for
+// the two halo rows) plus the row's window records, completing on the row's
+// `full` mbarrier.  Warp w relaxes segment column s0 + w of the current row
+// from shared memory and writes each result straight back to the global slot
+// it came from (the in-place rule of the pair; a slot is read and written
+// only by its own node, so whole ranges may be copied).  After every row the
+// block synchronises and warp 0 refills the slot of the row no step needs
+// any more, NS - 3 rows ahead of the rows being read.
+// ---------------------------------------------------------------------------
+namespace band {
+
+using staged::bulk_g2s;
+using staged::lds128;
+using staged::ldsf;
+using staged::mbar_arrive_expect;
+using staged::mbar_init;
+using staged::saddr;
+
+// Bounded wait on an mbarrier phase.  With a suspend-time hint each poll may
+// keep the thread suspended until the phase completes (up to the hint), so a
+// wait costs a poll or two instead of a spin.
+#ifndef LBM_BAND_WAIT_HINT_NS
+#define LBM_BAND_WAIT_HINT_NS 0
+#endif
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+#if LBM_BAND_WAIT_HINT_NS > 0
+    for (int i = 0; i < (1 << 16); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity), "n"(LBM_BAND_WAIT_HINT_NS)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+#else
+    return staged::mbar_wait(bar, parity);
+#endif
+}
+
+template <int S, int NS>
+struct Geo {
+    static constexpr int RANGE = 32 * S + 8;        // floats per (row, plane): 32 S + 2 nodes, widened to 16 B
+    static constexpr uint32_t RB = RANGE * 4;       // bytes per (row, plane)
+    static constexpr uint32_t WINB = 16 * S;        // window records of a row
+    static constexpr uint32_t SLOT = 9 * RB + WINB; // one staged row
+    static constexpr uint32_t RNGT = NS * SLOT;     // range table of the band
+    static constexpr uint32_t BARS = RNGT + (kBandRowsMax + 2) * 8;
+    static constexpr uint32_t SMEM = BARS + 2 * NS * 8;  // full, then empty barriers
+    static_assert(RB % 16 == 0 && SLOT % 16 == 0 && RNGT % 16 == 0, "16-byte aligned ring");
+};
+
+// Planes that stream out of the row above the band (c_y = +1) and out of the
+// row below it (c_y = -1).
+template <class L, int... Is>
+__host__ __device__ constexpr uint32_t planes_cy(int cy, std::integer_sequence<int, Is...>) {
+    return ((L::c(Is, 1) == cy ? (1u << Is) : 0u) | ...);
+}
+
+// Source of direction I: the global element the pull step reads (and the
+// gather step writes back), and the shared-memory address of its staged
+// copy.  rb[q]: shared address of row q's plane 0 minus 4 x its first staged
+// compact index (q = 0, 1, 2: rows y - 1, y, y + 1, clamped onto the domain).
+template <class L, int I>
+__device__ __forceinline__ void src_band(const Win (&w)[3], uint32_t PS, uint32_t RB, uint32_t kd, bool my,
+                                         const uint32_t (&rb)[3], uint32_t& e, uint32_t& sa) {
+    using d = Dir<I, L>;
+    const Win& wn = w[d::row];
+    const bool sf = win_fluid<d::cx>(wn);
+    const uint32_t k = win_idx<d::cx>(wn);
+    const uint32_t plane = (d::cy != 0 && my) ? (uint32_t)d::fy : (uint32_t)I;
+    e = sf ? plane * PS + k : (uint32_t)d::o * PS + kd;
+    sa = sf ? rb[d::row] + plane * RB + 4u * k : rb[1] + (uint32_t)d::o * RB + 4u * kd;
+}
+template <class L, int... Is>
+__device__ __forceinline__ void srcs_band(const Win (&w)[3], uint32_t PS, uint32_t RB, uint32_t kd, bool ylo,
+                                          bool yhi, const uint32_t (&rb)[3], uint32_t (&e)[L::Q],
+                                          uint32_t (&sa)[L::Q], std::integer_sequence<int, Is...>) {
+    (src_band<L, Is>(w, PS, RB, kd, Dir<Is, L>::cy > 0 ? ylo : yhi, rb, e[Is], sa[Is]), ...);
+}
+
+}  // namespace band
+
+template <class L, int EQ, int S, int NS>
+__global__ void __launch_bounds__((S + 1) * 32, 4) k_aa_gather_band(const __grid_constant__ HotArgs A) {
+    static_assert(L::Q == 9, "the band gather step is written for D2Q9");
+    static_assert(NS >= 3, "a step reads three staged rows");
+    using G = band::Geo<S, NS>;
+    constexpr int Q = L::Q;
+    constexpr uint32_t kUp = band::planes_cy<L>(1, std::make_integer_sequence<int, Q>{});
+    constexpr uint32_t kDown = band::planes_cy<L>(-1, std::make_integer_sequence<int, Q>{});
+    extern __shared__ __align__(128) unsigned char smb[];
+    __shared__ int failed;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint4 it = __ldg(A.bands + blockIdx.x);
+    const DomainDev* Dp = A.dom + it.x;
+    if (!__ldg(&Dp->active)) return;
+    const int ny = __ldg(&Dp->ny), nseg = __ldg(&Dp->nseg);
+    const uint32_t seg_base = __ldg(&Dp->seg_base);
+    const int y0 = (int)(it.y & 0xffffu), nrows = (int)(it.y >> 16);
+    const int s0 = (int)(it.z & 0xffffu), nsegs = (int)(it.z >> 16);
+    const int nstage = nrows + 2;
+    const uint32_t ring = band::saddr(smb), full0 = ring + G::BARS, empty0 = full0 + 8u * NS;
+    uint2* const rt = reinterpret_cast<uint2*>(smb + G::RNGT);
+    for (int j = threadIdx.x; j < nstage; j += blockDim.x) rt[j] = __ldg(A.band_rng + it.w + j);
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int k = 0; k < NS; ++k) {
+            band::mbar_init(full0 + 8u * k, 1);
+            band::mbar_init(empty0 + 8u * k, (uint32_t)nsegs);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t PS = A.pstride;
+    float* const g = A.dst[0];
+    int issued = 0;
+    if (wid == S) {
+        // Producer: stage row j (row y0 - 1 + j) into slot j % NS once every
+        // consumer has released the row that held it.  Lane 0 arms the slot's
+        // `full` barrier with the byte count first; a row outside the domain
+        // arms it with none, so its phase completes at once.
+#pragma unroll 1
+        for (int j = 0; j < nstage; ++j) {
+            const int slot = j % NS;
+            if (j >= NS) {
+                // release number j / NS - 1 of the slot: row j - NS
+                if (!band::mbar_wait(empty0 + 8u * slot, (uint32_t)(j / NS - 1) & 1u)) {
+                    if (lane == 0) atomicOr(&failed, 1);
+                    break;
+                }
+                // the consumers' reads of the slot come before the copy engine's writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            }
+            const int r = y0 - 1 + j;
+            const bool live = r >= 0 && r < ny;
+            const uint2 rr = rt[j];
+            const uint32_t pm = j == 0 ? kUp : (j == nrows + 1 ? kDown : (1u << Q) - 1u);
+            const uint32_t bytes = live ? (uint32_t)__popc(pm) * rr.y * 16u + (uint32_t)nsegs * 16u : 0u;
+            const uint32_t bar = full0 + 8u * slot, dst = ring + (uint32_t)slot * G::SLOT;
+            if (lane == 0) band::mbar_arrive_expect(bar, bytes);
+            __syncwarp();
+            if (live) {
+                if (lane < Q) {
+                    if (((pm >> lane) & 1u) && rr.y)
+                        band::bulk_g2s(dst + (uint32_t)lane * G::RB, g + (size_t)lane * PS + rr.x, rr.y * 16u, bar);
+                } else if (lane == Q) {
+                    band::bulk_g2s(dst + (uint32_t)Q * G::RB,
+                                   A.win + seg_base + (uint32_t)r * (uint32_t)nseg + (uint32_t)s0,
+                                   (uint32_t)nsegs * 16u, bar);
+                }
+            }
+            issued = j + 1;
+        }
+    } else if (wid < nsegs) {
+        const int nx = __ldg(&Dp->nx);
+        const int s = s0 + wid;
+        const int x = s * kSegW + lane;
+        const bool xin = (x == 0), xout = (x == nx - 1);
+        const bool edge = (s == 0) || (s == nseg - 1);
+        const float drho_in = __ldg(&Dp->drho_in), rho0 = __ldg(&Dp->rho0), om = __ldg(&Dp->omega),
+                    omm = __ldg(&Dp->omega_m);
+        const uint32_t lmask = (1u << lane) - 1u;
+        const uint32_t wofs = 9u * G::RB + (uint32_t)wid * 16u;
+        // slots and full-barrier parities of rows t (sm), t + 1 (sc), t + 2 (sp)
+        int sm = 0, sc = 1, sp = 2;
+        uint32_t pp = 0;
+        bool ok = band::mbar_wait(full0, 0) && band::mbar_wait(full0 + 8u, 0) && band::mbar_wait(full0 + 16u, 0);
+        Win w[3];
+        uint32_t rb[3];
+        if (ok) {
+            // rows y0 - 1, y0, y0 + 1, clamped onto the domain (a clamped row is row y0 itself)
+            const int km = y0 == 0 ? sc : sm, kp = y0 + 1 >= ny ? sc : sp;
+            const int jm = y0 == 0 ? 1 : 0, jp = y0 + 1 >= ny ? 1 : 2;
+            w[0] = make_win(band::lds128(ring + (uint32_t)km * G::SLOT + wofs), lane, lmask);
+            w[1] = make_win(band::lds128(ring + (uint32_t)sc * G::SLOT + wofs), lane, lmask);
+            w[2] = make_win(band::lds128(ring + (uint32_t)kp * G::SLOT + wofs), lane, lmask);
+            rb[0] = ring + (uint32_t)km * G::SLOT - 4u * rt[jm].x;
+            rb[1] = ring + (uint32_t)sc * G::SLOT - 4u * rt[1].x;
+            rb[2] = ring + (uint32_t)kp * G::SLOT - 4u * rt[jp].x;
+        }
+#pragma unroll 1
+        for (int t = 0; t < nrows && ok; ++t) {
+            const int y = y0 + t;
+            const bool fl = win_fluid<0>(w[1]);
+            const uint32_t kd = win_idx<0>(w[1]);
+            uint32_t e[Q], sa[Q];
+            band::srcs_band<L>(w, PS, G::RB, kd, y == 0, y == ny - 1, rb, e, sa, std::make_integer_sequence<int, Q>{});
+            float f[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = band::ldsf(sa[i]);
+            relax<L, EQ>(f, edge, xin, xout, drho_in, rho0, om, omm);
+            if (fl) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    if (chk_store(e[opp<L>(i)], (uint32_t)Q * PS, A.err)) g[e[opp<L>(i)]] = f[i];
+            }
+            // row t is read by no later step of this warp
+            __syncwarp();
+            if (lane == 0) staged::mbar_arrive(empty0 + 8u * sm);
+            if (t + 1 == nrows) break;
+            sm = sc;
+            sc = sp;
+            if (++sp == NS) {
+                sp = 0;
+                pp ^= 1u;
+            }
+            // next row y + 2 (row t + 3 of the band), unless y + 1 is the domain's last row
+            const int jn = t + 3;
+            if (!band::mbar_wait(full0 + 8u * sp, pp)) {
+                ok = false;
+                if (lane == 0) atomicOr(&failed, 1);
+                break;
+            }
+            w[0] = w[1];
+            w[1] = w[2];
+            rb[0] = rb[1];
+            rb[1] = rb[2];
+            const int kn = (y + 2 >= ny) ? sc : sp;
+            w[2] = make_win(band::lds128(ring + (uint32_t)kn * G::SLOT + wofs), lane, lmask);
+            rb[2] = ring + (uint32_t)kn * G::SLOT - 4u * rt[(y + 2 >= ny) ? jn - 1 : jn].x;
+        }
+        if (!ok && lane == 0) atomicOr(&failed, 1);
+    }
+    __syncthreads();
+    if (failed && wid == S && lane == 0) {
+        // a copy or a release never completed: report it and give the staged
+        // rows still in flight one more bounded wait before the block exits
+        atomicOr(A.err, 1u);
+        for (int j = max(0, issued - NS); j < issued; ++j) band::mbar_wait(full0 + 8u * (j % NS), (uint32_t)(j / NS) & 1u);
+    }
+}
+
 // Local step of the pair: own slots only, pre-collision f_j from slot opp(j),
 // post-collision f*_j to slot j.  It needs no geometry, so it runs over the
 // compact index directly: each lane takes V consecutive slots as one aligned
@@ -847,6 +1094,34 @@ static cudaError_t staged_dispatch(int rows, const HotArgs& A, cudaStream_t st) 
     return cudaErrorInvalidValue;
 }
 
+// Staged rows of the band gather step's ring (3 in use, the rest in flight).
+#ifndef LBM_BAND_STAGES
+#define LBM_BAND_STAGES 5
+#endif
+// Band gather step: one block per band.
+template <class L, int EQ>
+static cudaError_t band_launch(const HotArgs& A, cudaStream_t st) {
+    if constexpr (L::Q != 9) {
+        return cudaErrorInvalidValue;
+    } else {
+        using G = band::Geo<kBandSegs, LBM_BAND_STAGES>;
+        if (A.nbands == 0) return cudaSuccess;
+        auto kern = k_aa_gather_band<L, EQ, kBandSegs, LBM_BAND_STAGES>;
+        static std::atomic<uint64_t> attr_set{0};  // bit d: attribute set on device d
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const uint64_t bit = 1ull << (dev & 63);
+        if (dev >= 64 || !(attr_set.load() & bit)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) attr_set.fetch_or(bit);
+        }
+        kern<<<A.nbands, (kBandSegs + 1) * 32, G::SMEM, st>>>(A);
+        return cudaGetLastError();
+    }
+}
+
 // Row batches of the direct gather step a launch configuration may choose.
 template <class L>
 struct GatherBatches {
@@ -882,6 +1157,7 @@ static cudaError_t gather_direct_launch(int threads, const HotArgs& A, cudaStrea
 template <class L, int EQ>
 static cudaError_t aa_half_launch(int half, const StepLaunch& cfg, const HotArgs& A, cudaStream_t st) {
     const int threads = cfg.threads > 0 ? cfg.threads : 128;
+    if (half == 0 && cfg.band_rows > 0) return band_launch<L, EQ>(A, st);
     if (half == 0 && cfg.tile_rows > 0) return staged_dispatch<L, EQ>(cfg.tile_rows, A, st);
     if (half == 0) {
         const int rs = cfg.gather_batch > 0 ? cfg.gather_batch : GatherSmem<L>::rows;
@@ -911,6 +1187,7 @@ cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch&
 }
 
 int staged_gather_lattice(int q) { return q == 9; }
+int band_gather_lattice(int q) { return q == 9; }
 
 void gather_batches(int q, int* lo, int* hi, int* def) {
     *lo = q == 9 ? GatherBatches<D2Q9>::lo : GatherBatches<D3Q19>::lo;

@@ -105,6 +105,18 @@ struct lbm_solver {
     GatherTile* d_tiles = nullptr;  // staged gather step: tile list
     uint32_t ntiles = 0;
     int tile_rows = 0;              // rows per tile of the staged gather step (0: direct gather step)
+    BandItem* d_bands = nullptr;    // band gather step: band list and range records
+    uint2* d_band_rng = nullptr;
+    uint32_t nbands = 0;
+    int band_rows = 0;              // rows per band of the band gather step (0: not used)
+    // L2-blocked pairs: the plain steps of a pair run block by block -- gather
+    // step of block k + 1, then local step of block k -- so that each block's
+    // populations are still in L2 when its local step reads them.  blk_item[k]
+    // / blk_vitem[k]: first strip / local-step item of block k (K + 1 entries;
+    // empty: one block, the plain pair).
+    int pair_block_mb = 0;
+    std::vector<uint32_t> blk_item, blk_vitem;
+    std::vector<uint4> h_items;     // host copy of the strip work list
     int gather_batch = 0;           // rows in flight per warp of the direct gather step (0: default)
     int strip_rows = 8;             // rows per strip work item
     std::vector<uint32_t> h_off, h_smask;  // segment offsets and fluid masks (host copies)
@@ -141,7 +153,7 @@ struct lbm_solver {
         G.pstride = pstride;
         return G;
     }
-    StepLaunch launch_cfg() const { return StepLaunch{opt.block_threads, tile_rows, gather_batch}; }
+    StepLaunch launch_cfg() const { return StepLaunch{opt.block_threads, tile_rows, gather_batch, band_rows}; }
     HotArgs hot() const {
         HotArgs A;
         A.dom = d_dom;
@@ -155,6 +167,9 @@ struct lbm_solver {
         A.tiles = d_tiles;
         A.ntiles = ntiles;
         A.err = err_word();
+        A.bands = d_bands;
+        A.nbands = nbands;
+        A.band_rng = d_band_rng;
         return A;
     }
     // device error word, kept right after the observables so that every
@@ -260,6 +275,8 @@ void free_solver(lbm_handle h) {
         dfree(h, h->d_vitems);
         dfree(h, h->d_face);
         dfree(h, h->d_tiles);
+        dfree(h, h->d_bands);
+        dfree(h, h->d_band_rng);
         for (auto& p : h->d_col) dfree(h, p);
         dfree(h, h->d_mask);
         dfree(h, h->d_g[0]);
@@ -346,9 +363,46 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
         }
         plain = 0;
     } else if (h->opt.in_place_pairs) {
+        const StepLaunch cfg = h->launch_cfg();
+        const size_t K = h->blk_item.empty() ? 0 : h->blk_item.size() - 1;
+        const bool blocked = K >= 2 && cfg.tile_rows <= 0 && cfg.band_rows <= 0;
+        auto gather_of = [&](size_t k) {
+            HotArgs B = A;
+            B.items = A.items + h->blk_item[k];
+            B.nitems = h->blk_item[k + 1] - h->blk_item[k];
+            return B;
+        };
+        auto local_of = [&](size_t k) {
+            HotArgs B = A;
+            B.vitems = A.vitems + h->blk_vitem[k];
+            B.nvitems = h->blk_vitem[k + 1] - h->blk_vitem[k];
+            return B;
+        };
         for (; plain >= 2; plain -= 2) {
+            if (blocked) {
+                // gather step of block k, then local step of block k - 1
+                for (size_t k = 0; k <= K; ++k) {
+                    if (k < K) {
+                        if (prof) CK(h, prof->mark(h->st));
+                        CK(h, launch_aa_half(h->q, h->eq, 0, gather_of(k), h->d_g[h->cur], cfg, h->st));
+                        if (prof) {
+                            CK(h, prof->mark(h->st));
+                            prof->kind.push_back(0);
+                        }
+                    }
+                    if (k >= 1) {
+                        if (prof) CK(h, prof->mark(h->st));
+                        CK(h, launch_aa_half(h->q, h->eq, 1, local_of(k - 1), h->d_g[h->cur], cfg, h->st));
+                        if (prof) {
+                            CK(h, prof->mark(h->st));
+                            prof->kind.push_back(1);
+                        }
+                    }
+                }
+                continue;
+            }
             if (!prof) {
-                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], h->launch_cfg(), h->st));
+                CK(h, launch_aa_pair(h->q, h->eq, A, h->d_g[h->cur], cfg, h->st));
                 continue;
             }
             for (int half = 0; half < 2; ++half) {
@@ -587,6 +641,8 @@ void lbm_options_default(lbm_options* o) {
     o->in_place_pairs = 1;
     o->collision = LBM_COLL_BGK;
     o->trt_lambda = 3.0 / 16.0;
+    o->band_rows = 0;
+    o->pair_block_mb = 0;
 }
 
 lbm_status lbm_qsgs(uint64_t seed, int32_t nx, int32_t ny, int32_t nz, double core_p, double porosity,
@@ -667,6 +723,7 @@ lbm_status build_items(lbm_handle h, int R) {
         G.nitems = (uint32_t)items.size() - G.item_base;
     }
     dfree(h, h->d_items);
+    h->h_items = items;
     h->nitems = (uint32_t)items.size();
     CK(h, dmalloc(h, &h->d_items, sizeof(uint4) * std::max<size_t>(items.size(), 1)));
     CK(h, cudaMemcpyAsync(h->d_items, items.data(), sizeof(uint4) * items.size(), cudaMemcpyHostToDevice, h->st));
@@ -736,6 +793,120 @@ lbm_status build_tiles(lbm_handle h, int tr) {
     return LBM_OK;
 }
 
+// Bands of the band gather step (D2Q9 in-place pairs): per domain, runs of up
+// to br rows at each piece of the width -- the domain's segment columns split
+// into ceil(nseg / kBandSegs) pieces as even as possible -- pieces innermost;
+// all-solid bands are left out.  Range records for the rows y0 - 1 ..
+// y0 + nrows of each band: the 16-byte aligned compact range covering nodes
+// 32 s0 - 1 .. 32 (s0 + nsegs) (length 0 for a row outside the domain or
+// without fluid there).  br = 0 drops the list.
+lbm_status build_bands(lbm_handle h, int br) {
+    const int n = (int)h->dom.size();
+    if (br && (!band_gather_lattice(h->q) || !h->opt.in_place_pairs || h->forced || h->slab)) br = 0;
+    for (int d = 0; d < n && br; ++d)
+        if (h->hdom[d].nseg > 65535 || h->hdom[d].ny > 65535 || h->hdom[d].nz != 1) br = 0;
+    const std::vector<uint32_t>& smask = h->h_smask;
+    const std::vector<uint32_t>& off = h->h_off;
+    std::vector<uint4> bands;
+    std::vector<uint2> rng;
+    for (int d = 0; d < n && br; ++d) {
+        const DomainDev& G = h->hdom[d];
+        const int pieces = (G.nseg + kBandSegs - 1) / kBandSegs;
+        auto seg = [&](int y, int sx) { return G.seg_base + (uint32_t)y * (uint32_t)G.nseg + (uint32_t)sx; };
+        for (int y0 = 0; y0 < G.ny; y0 += br)
+            for (int p = 0, s0 = 0; p < pieces; ++p) {
+                const int ns = G.nseg / pieces + (p < G.nseg % pieces ? 1 : 0);
+                const int nr = std::min(br, G.ny - y0);
+                bool any = false;
+                for (int r = 0; r < nr && !any; ++r)
+                    for (int k = 0; k < ns && !any; ++k) any = smask[seg(y0 + r, s0 + k)] != 0u;
+                if (any) {
+                    bands.push_back(make_uint4((uint32_t)d, (uint32_t)y0 | ((uint32_t)nr << 16),
+                                               (uint32_t)s0 | ((uint32_t)ns << 16), (uint32_t)rng.size()));
+                    for (int r = y0 - 1; r <= y0 + nr; ++r) {
+                        if (r < 0 || r >= G.ny) {
+                            rng.push_back(make_uint2(0u, 0u));
+                            continue;
+                        }
+                        const uint32_t g0 = seg(r, s0), g1 = seg(r, s0 + ns - 1);
+                        const uint32_t left = s0 > 0 ? (smask[g0 - 1] >> 31) & 1u : 0u;
+                        const uint32_t right = s0 + ns < G.nseg ? smask[g1 + 1] & 1u : 0u;
+                        const uint32_t lo = off[g0] - left;
+                        const uint32_t hi = off[g1] + (uint32_t)__builtin_popcount(smask[g1]) + right;
+                        const uint32_t a0 = lo & ~3u, a1 = (hi + 3u) & ~3u;
+                        rng.push_back(make_uint2(a0, hi > lo ? (a1 - a0) / 4u : 0u));
+                    }
+                }
+                s0 += ns;
+            }
+    }
+    dfree(h, h->d_bands);
+    dfree(h, h->d_band_rng);
+    h->band_rows = br;
+    h->nbands = (uint32_t)bands.size();
+    if (br) {
+        CK(h, dmalloc(h, &h->d_bands, sizeof(uint4) * std::max<size_t>(bands.size(), 1)));
+        CK(h, dmalloc(h, &h->d_band_rng, sizeof(uint2) * std::max<size_t>(rng.size(), 1)));
+        CK(h, cudaMemcpyAsync(h->d_bands, bands.data(), sizeof(uint4) * bands.size(), cudaMemcpyHostToDevice, h->st));
+        CK(h, cudaMemcpyAsync(h->d_band_rng, rng.data(), sizeof(uint2) * rng.size(), cudaMemcpyHostToDevice, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+    }
+    return LBM_OK;
+}
+
+// Blocks of the L2-blocked pairs: consecutive runs of the strip list holding
+// about mb MB of populations each, cut only where the local step of one block
+// can follow the gather step of the next -- between row groups of a 2D domain,
+// between z planes of a 3D one, or between domains.  Local-step items go to
+// the block holding their last slot: a slot's writers in the gather step are
+// its own row and the neighbouring rows (planes in 3D), so every writer of a
+// block-k item lies in blocks <= k + 1.  mb = 0 drops the blocks.
+lbm_status build_pair_blocks(lbm_handle h, int mb) {
+    h->blk_item.clear();
+    h->blk_vitem.clear();
+    h->pair_block_mb = 0;
+    if (mb <= 0 || !h->opt.in_place_pairs || h->forced || h->slab) return LBM_OK;
+    const uint64_t target = std::max<uint64_t>((uint64_t)mb << 20, 1) / (4ull * (uint64_t)h->q);
+    std::vector<uint32_t> cstart;  // compact index where each block begins
+    uint32_t prev_d = ~0u, prev_z = ~0u, prev_y = ~0u;
+    uint64_t block_c0 = 0;
+    for (uint32_t i = 0; i < (uint32_t)h->h_items.size(); ++i) {
+        const uint4 it = h->h_items[i];
+        const uint32_t d = it.y & 0xffffffu, y0 = it.z & 0xffffu, z = it.z >> 16;
+        if (d == prev_d && z == prev_z && y0 == prev_y) continue;
+        const DomainDev& G = h->hdom[d];
+        const bool cut_ok = d != prev_d || (G.nz == 1 ? y0 != prev_y : z != prev_z);
+        const uint32_t c = h->h_off[G.seg_base + ((uint32_t)z * (uint32_t)G.ny + y0) * (uint32_t)G.nseg];
+        if (h->blk_item.empty() || (cut_ok && (uint64_t)c - block_c0 >= target)) {
+            h->blk_item.push_back(i);
+            cstart.push_back(h->blk_item.size() == 1 ? 0u : c);
+            block_c0 = c;
+        }
+        prev_d = d;
+        prev_z = z;
+        prev_y = y0;
+    }
+    h->pair_block_mb = mb;
+    if (h->blk_item.size() < 2) {  // one block: whole-batch pairs
+        h->blk_item.clear();
+        return LBM_OK;
+    }
+    h->blk_item.push_back((uint32_t)h->h_items.size());
+    // local-step items, in the order the create call made them
+    const uint32_t span = 32u * (uint32_t)local_step_vector(h->q);
+    const size_t K = cstart.size();
+    h->blk_vitem.assign(K + 1, 0u);
+    uint32_t j = 0;
+    size_t k = 0;
+    for (size_t d = 0; d < h->hdom.size(); ++d)
+        for (uint32_t c = h->hdom[d].fluid_begin; c < h->hdom[d].fluid_end; c += span, ++j) {
+            const uint32_t last = std::min(c + span, h->hdom[d].fluid_end) - 1u;
+            while (k + 1 < K && cstart[k + 1] <= last) h->blk_vitem[++k] = j;
+        }
+    while (k + 1 <= K) h->blk_vitem[++k] = j;
+    return LBM_OK;
+}
+
 // Compact indices of a slab's exchanged columns, fluid nodes in (z, y) order.
 lbm_status build_slab_columns(lbm_handle h) {
     const DomainDev& G = h->hdom[0];
@@ -785,6 +956,8 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         (o.in_place_pairs != 0 && o.in_place_pairs != 1) ||
         (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT) ||
         !(o.trt_lambda > 0.0 && std::isfinite(o.trt_lambda)) || o.tile_rows < -1 || o.tile_rows > kTileRowsMax ||
+        o.band_rows < -1 || o.band_rows > kBandRowsMax || (o.tile_rows > 0 && o.band_rows > 0) ||
+        o.pair_block_mb < -1 || o.pair_block_mb > kPairBlockMbMax ||
         (o.autotune != 0 && o.autotune != 1) || o.gather_batch < 0 || (!o.alloc_fn != !o.free_fn))
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (slab) o.in_place_pairs = 0;  // a slab's ghost columns are refreshed between single pull steps
@@ -959,6 +1132,10 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
     {
         lbm_status bs = build_items(h, o.strip_rows > 0 ? o.strip_rows : 8);
         if (bs == LBM_OK) bs = build_tiles(h, o.tile_rows > 0 ? o.tile_rows : 0);
+        if (bs == LBM_OK) bs = build_bands(h, o.band_rows > 0 ? o.band_rows : (o.band_rows == 0 && o.tile_rows <= 0 ? kBandRowsDefault : 0));
+        if (bs == LBM_OK)
+            bs = build_pair_blocks(h, o.pair_block_mb > 0 ? o.pair_block_mb
+                                                          : (o.pair_block_mb == 0 ? kPairBlockMbDefault : 0));
         if (bs == LBM_OK && slab) bs = build_slab_columns(h);
         if (bs != LBM_OK) {
             free_solver(h);
@@ -1710,6 +1887,8 @@ lbm_launch current_launch(lbm_handle h) {
     c.strip_rows = h->strip_rows;
     c.gather_batch = h->gather_batch > 0 ? h->gather_batch : def;
     c.tile_rows = h->tile_rows;
+    c.band_rows = h->band_rows;
+    c.pair_block_mb = h->pair_block_mb;
     return c;
 }
 
@@ -1718,7 +1897,9 @@ bool launch_valid(lbm_handle h, const lbm_launch& c) {
     gather_batches(h->q, &lo, &hi, &def);
     return c.block_threads >= 32 && c.block_threads <= 256 && c.block_threads % 32 == 0 && c.strip_rows >= 1 &&
            c.strip_rows <= 255 && (c.gather_batch == lo || c.gather_batch == hi) && c.tile_rows >= 0 &&
-           c.tile_rows <= kTileRowsMax && (c.tile_rows == 0 || staged_gather_lattice(h->q));
+           c.tile_rows <= kTileRowsMax && (c.tile_rows == 0 || staged_gather_lattice(h->q)) && c.band_rows >= 0 &&
+           c.band_rows <= kBandRowsMax && (c.band_rows == 0 || band_gather_lattice(h->q)) &&
+           !(c.tile_rows > 0 && c.band_rows > 0) && c.pair_block_mb >= 0 && c.pair_block_mb <= kPairBlockMbMax;
 }
 
 lbm_status apply_launch(lbm_handle h, const lbm_launch& c) {
@@ -1727,6 +1908,9 @@ lbm_status apply_launch(lbm_handle h, const lbm_launch& c) {
     lbm_status s = LBM_OK;
     if (c.strip_rows != cur.strip_rows) s = build_items(h, c.strip_rows);
     if (s == LBM_OK && c.tile_rows != cur.tile_rows) s = build_tiles(h, c.tile_rows);
+    if (s == LBM_OK && c.band_rows != cur.band_rows) s = build_bands(h, c.band_rows);
+    if (s == LBM_OK && (c.pair_block_mb != cur.pair_block_mb || c.strip_rows != cur.strip_rows))
+        s = build_pair_blocks(h, c.pair_block_mb);
     if (s != LBM_OK) return s;
     h->opt.block_threads = c.block_threads;
     h->gather_batch = c.gather_batch;
@@ -1778,13 +1962,17 @@ std::map<std::string, CacheEntry> read_cache(const char* path) {
             f = std::strchr(f + std::strlen(name), ':');
             return f && std::sscanf(f + 1, "%lf", v) == 1;
         };
-        double bt, sr, gb, tr, us;
+        double bt, sr, gb, tr, us, br = 0.0, pb = 0.0;
         if (field("\"block_threads\"", &bt) && field("\"strip_rows\"", &sr) && field("\"gather_batch\"", &gb) &&
             field("\"tile_rows\"", &tr) && field("\"us_per_step\"", &us)) {
+            field("\"band_rows\"", &br);  // absent in entries written before band gather steps existed
+            field("\"pair_block_mb\"", &pb);
             e.c.block_threads = (int32_t)bt;
             e.c.strip_rows = (int32_t)sr;
             e.c.gather_batch = (int32_t)gb;
             e.c.tile_rows = (int32_t)tr;
+            e.c.band_rows = (int32_t)br;
+            e.c.pair_block_mb = (int32_t)pb;
             e.us = us;
             m[key] = e;
         }
@@ -1804,9 +1992,9 @@ bool write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
         const CacheEntry& e = kv.second;
         ok = ok && std::fprintf(fp,
                                 "\"%s\": {\"block_threads\": %d, \"strip_rows\": %d, \"gather_batch\": %d, "
-                                "\"tile_rows\": %d, \"us_per_step\": %.3f}%s\n",
+                                "\"tile_rows\": %d, \"band_rows\": %d, \"pair_block_mb\": %d, \"us_per_step\": %.3f}%s\n",
                                 kv.first.c_str(), e.c.block_threads, e.c.strip_rows, e.c.gather_batch, e.c.tile_rows,
-                                e.us, ++i < m.size() ? "," : "") > 0;
+                                e.c.band_rows, e.c.pair_block_mb, e.us, ++i < m.size() ? "," : "") > 0;
     }
     ok = ok && std::fprintf(fp, "}\n") > 0;
     ok = (std::fclose(fp) == 0) && ok;
@@ -1914,7 +2102,10 @@ lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lb
     int lo, hi, def;
     gather_batches(h->q, &lo, &hi, &def);
     lbm_tune_result r{};
-    r.defaults = lbm_launch{128, 8, def, 0};
+    const bool bands_apply = band_gather_lattice(h->q) && h->opt.in_place_pairs && !h->forced && !h->slab;
+    const bool blocks_apply = h->opt.in_place_pairs && !h->forced && !h->slab;
+    r.defaults = lbm_launch{128, 8, def, 0, bands_apply ? kBandRowsDefault : 0,
+                            blocks_apply ? kPairBlockMbDefault : 0};
     r.chosen = current_launch(h);
     if (h->forced) {  // pull steps of the periodic kernel only: nothing to choose
         if (out) *out = r;
@@ -1940,11 +2131,16 @@ lbm_status lbm_autotune(lbm_handle h, const char* cache_path, int32_t nsteps, lb
     for (int bt : {64, 128, 256})
         for (int sr : {4, 8, 16})
             for (int gb : {lo, hi}) {
-                const lbm_launch c{bt, sr, gb, 0};
+                const lbm_launch c{bt, sr, gb, 0, 0};
                 if (std::memcmp(&c, &r.defaults, sizeof(c)) != 0) cands.push_back(c);
             }
-    if (staged_gather_lattice(h->q) && h->opt.in_place_pairs)
-        for (int tr : {2, 3}) cands.push_back(lbm_launch{128, 8, def, tr});
+    if (staged_gather_lattice(h->q) && h->opt.in_place_pairs && !h->slab)
+        for (int tr : {2, 3}) cands.push_back(lbm_launch{128, 8, def, tr, 0});
+    if (bands_apply)
+        for (int br : {16, 32, 64}) {
+            const lbm_launch c{128, 8, def, 0, br};
+            if (std::memcmp(&c, &r.defaults, sizeof(c)) != 0) cands.push_back(c);
+        }
     double best = INFINITY;
     lbm_launch best_c = r.defaults;
     for (size_t i = 0; i < cands.size(); ++i) {

@@ -122,6 +122,25 @@ struct GatherTile {
 };
 static_assert(sizeof(GatherTile) == 128, "GatherTile is 128 bytes");
 
+// Band of the band gather step (D2Q9): up to kBandSegs consecutive segment
+// columns s0 .. s0 + nsegs - 1 of one domain and up to kBandRowsMax rows
+// y0 .. y0 + nrows - 1, walked top to bottom by one block.
+//   x = domain; y = y0 | nrows << 16; z = s0 | nsegs << 16;
+//   w = index of the band's first range record.
+// Range records (one per row y0 - 1 .. y0 + nrows, rows outside the domain
+// included): x = first compact index of the row's staged range, a multiple of
+// 4; y = its length in 16-byte units (0: nothing to stage).  The range covers
+// the compact slots of nodes x = 32 s0 - 1 .. 32 (s0 + nsegs) of the row.
+using BandItem = uint4;
+constexpr int kBandSegs = 8;
+constexpr int kBandRowsMax = 64;
+// Rows per band when lbm_options.band_rows is 0 (0: the direct gather step).
+constexpr int kBandRowsDefault = 0;
+// L2-blocked pairs: MB of populations per block when lbm_options.pair_block_mb
+// is 0 (0: unblocked pairs), and the largest block size accepted.
+constexpr int kPairBlockMbDefault = 0;
+constexpr int kPairBlockMbMax = 4096;
+
 // Arguments of the hot stream-collide kernel.
 struct HotArgs {
     const DomainDev* dom;
@@ -137,6 +156,9 @@ struct HotArgs {
     const GatherTile* tiles; // staged gather step: tile list
     uint32_t ntiles;
     uint32_t* err;           // device error word (bit 0: a staged copy never completed)
+    const BandItem* bands;   // band gather step: band list
+    uint32_t nbands;
+    const uint2* band_rng;   // band gather step: range records
 };
 
 // Arguments shared by every segment kernel.

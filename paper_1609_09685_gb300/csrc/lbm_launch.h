@@ -17,6 +17,7 @@ struct StepLaunch {
     int threads;       // block size of the direct gather, local and pull steps (0 = 128)
     int tile_rows;     // > 0: staged gather step over A.tiles (built with that many rows per tile)
     int gather_batch;  // rows of loads in flight per warp of the direct gather step (0 = default)
+    int band_rows;     // > 0: band gather step over A.bands (built with up to that many rows per band)
 };
 // Two steps in place on g (gather step, then local step); see k_aa_gather.
 cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
@@ -24,6 +25,8 @@ cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch&
 cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
 // Nonzero when the lattice with q directions has a staged gather step.
 int staged_gather_lattice(int q);
+// Nonzero when the lattice with q directions has a band gather step.
+int band_gather_lattice(int q);
 // Row batches of the direct gather step: the two compiled ones and the default.
 void gather_batches(int q, int* lo, int* hi, int* def);
 // Slots per lane of the local step (its work items cover 32 x this many slots).

@@ -68,6 +68,8 @@ class lbm_options(C.Structure):
         ("alloc_fn", C.c_void_p),
         ("free_fn", C.c_void_p),
         ("alloc_ctx", C.c_void_p),
+        ("band_rows", C.c_int32),
+        ("pair_block_mb", C.c_int32),
     ]
 
 
@@ -104,7 +106,7 @@ def torch_allocator(fail_after: Optional[int] = None, log: Optional[list] = None
 
 class lbm_launch(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("strip_rows", C.c_int32), ("gather_batch", C.c_int32),
-                ("tile_rows", C.c_int32)]
+                ("tile_rows", C.c_int32), ("band_rows", C.c_int32), ("pair_block_mb", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -254,7 +256,7 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
                  stall_floor=1e-5, rho_out=1.0, stream=None, block_threads=0,
                  use_graphs=True, cancel_flag=None, strip_rows=0, k_tol=1e-5,
                  in_place_pairs=True, collision=0, trt_lambda=3.0 / 16.0, tile_rows=0, gather_batch=0,
-                 autotune=False, tune_cache=None, allocator=None) -> lbm_options:
+                 autotune=False, tune_cache=None, allocator=None, band_rows=0, pair_block_mb=0) -> lbm_options:
     o = lbm_options()
     load().lbm_options_default(C.byref(o))
     o.equilibrium = equilibrium
@@ -273,6 +275,8 @@ def make_options(equilibrium=LBM_EQ_QUADRATIC, check_interval=100, stall_checks=
     o.trt_lambda = trt_lambda
     o.tile_rows = tile_rows
     o.gather_batch = gather_batch
+    o.band_rows = band_rows
+    o.pair_block_mb = pair_block_mb
     o.autotune = 1 if autotune else 0
     o.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
     if allocator is not None:  # (alloc_fn, free_fn) callbacks, kept alive by the options object
@@ -585,8 +589,9 @@ def lbm_get_launch(s: Solver) -> dict:
     return c.as_dict()
 
 
-def lbm_set_launch(s: Solver, block_threads: int, strip_rows: int, gather_batch: int, tile_rows: int = 0) -> None:
-    c = lbm_launch(block_threads, strip_rows, gather_batch, tile_rows)
+def lbm_set_launch(s: Solver, block_threads: int, strip_rows: int, gather_batch: int, tile_rows: int = 0,
+                   band_rows: int = 0, pair_block_mb: int = 0) -> None:
+    c = lbm_launch(block_threads, strip_rows, gather_batch, tile_rows, band_rows, pair_block_mb)
     _check(load().lbm_set_launch(s.handle, C.byref(c)), s.handle)
 
 
@@ -628,7 +633,8 @@ def lbm_tune_cache_get(path: str, key: str):
 
 
 def lbm_tune_cache_put(path: str, key: str, cfg: dict, us_per_step: float) -> None:
-    c = lbm_launch(cfg["block_threads"], cfg["strip_rows"], cfg["gather_batch"], cfg["tile_rows"])
+    c = lbm_launch(cfg["block_threads"], cfg["strip_rows"], cfg["gather_batch"], cfg["tile_rows"],
+                   cfg.get("band_rows", 0), cfg.get("pair_block_mb", 0))
     _check(load().lbm_tune_cache_put(os.fsencode(path), key.encode(), C.byref(c), float(us_per_step)))
 
 

@@ -199,6 +199,16 @@ def test_tile_rows_option_is_validated(lib):
         assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
 
 
+def test_band_rows_option_is_validated(lib):
+    """band_rows in -1..64, and not together with a staged tile height."""
+    m = np.zeros((6, 9), np.uint8)
+    h = C.c_void_p()
+    for kw in (dict(band_rows=-2), dict(band_rows=65), dict(band_rows=8, tile_rows=2), dict(pair_block_mb=-2),
+               dict(pair_block_mb=4097)):
+        o = lbm.make_options(**kw)
+        assert lib.lbm_create_domain(m.ctypes.data, 9, 6, 0.8, 1e-3, C.byref(o), C.byref(h)) == lbm.LBM_ERR_ARG
+
+
 def test_tune_key_format(lib):
     """Key = device (spaces -> '_') | Q | floor(log2 fluid nodes) | equilibrium |
     collision | hash of the kernel sources."""
@@ -214,8 +224,8 @@ def test_tune_key_format(lib):
 def test_tune_cache_round_trip(lib, tmp_path):
     path = str(tmp_path / "tune.json")
     assert lbm.lbm_tune_cache_get(path, "k1") is None  # missing file = empty cache
-    a = dict(block_threads=64, strip_rows=16, gather_batch=2, tile_rows=0)
-    b = dict(block_threads=256, strip_rows=4, gather_batch=4, tile_rows=3)
+    a = dict(block_threads=64, strip_rows=16, gather_batch=2, tile_rows=0, band_rows=32, pair_block_mb=0)
+    b = dict(block_threads=256, strip_rows=4, gather_batch=4, tile_rows=3, band_rows=0, pair_block_mb=24)
     lbm.lbm_tune_cache_put(path, "k1", a, 301.25)
     lbm.lbm_tune_cache_put(path, "GPU A|q9|n2^20|eq0|coll0|abc", b, 12.5)
     assert lbm.lbm_tune_cache_get(path, "k1") == (a, 301.25)
@@ -229,6 +239,11 @@ def test_tune_cache_round_trip(lib, tmp_path):
         fh.write("not json at all\n\"k2\": {\"block_threads\": \n")
     assert lbm.lbm_tune_cache_get(path, "k2") is None
     assert lbm.lbm_tune_cache_get(path, "k1") == (b, 99.0)
+    with open(path, "a") as fh:  # an entry without band_rows reads as 0
+        fh.write('"k3": {"block_threads": 64, "strip_rows": 8, "gather_batch": 4, "tile_rows": 0, '
+                 '"us_per_step": 5.0}\n')
+    assert lbm.lbm_tune_cache_get(path, "k3") == (dict(a, strip_rows=8, gather_batch=4, band_rows=0), 5.0)
+    # an entry without band_rows / pair_block_mb reads them as 0
     cfg = lbm.lbm_launch(128, 8, 4, 0)
     assert lib.lbm_tune_cache_put(path.encode(), b'bad"key', C.byref(cfg), 1.0) == lbm.LBM_ERR_ARG
     assert lib.lbm_tune_cache_put(str(tmp_path / "no" / "dir.json").encode(), b"k", C.byref(cfg), 1.0) == lbm.LBM_ERR_IO

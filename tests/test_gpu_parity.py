@@ -225,6 +225,109 @@ def test_staged_gather_matches_direct_gather_bitwise():
             assert np.array_equal(runs[-1][1], runs[rows][1])
 
 
+def test_band_gather_matches_direct_gather_bitwise():
+    """The band gather step (a block walks down a band of rows, staging each
+    row's compact range of every plane in a shared-memory ring by bulk copies)
+    and the direct one (per-node loads) do the same arithmetic on the same
+    values: after in-place pairs from the initial state and from a random
+    state, populations and observables are bit-identical.  Masks: the small
+    ragged, 32-multiple, single-row and channel cases, plus domains wide enough
+    to be cut into two and three pieces of the width (a solid block, a fluid
+    column on a piece edge), for band heights from one row to the maximum."""
+    rng = np.random.default_rng(11)
+    masks = list(_masks_2d().values())
+    w1 = (rng.random((21, 530)) < 0.3).astype(np.uint8)  # 17 segments: pieces of 9 and 8
+    w1[:, 288] = 0  # fluid column on the piece edge (x = 32 * 9)
+    w1[5:9, 100:200] = 1
+    masks.append(w1)
+    w2, _ = O.qsgs((37, 1100), 4, 0.02, 0.7)  # 35 segments: pieces of 12, 12, 11
+    masks.append(w2)
+    w3 = np.zeros((70, 65), np.uint8)  # 3 segments, 70 rows: several bands per column
+    w3[10:20, 30:40] = 1
+    masks.append(w3)
+    taus = [0.6 + 0.07 * i for i in range(len(masks))]
+    drhos = [1e-3] * len(masks)
+    for eq in (0, 1):
+        runs = {}
+        for rows in (-1, 1, 2, 5, 32, 64):
+            opts = lbm.make_options(equilibrium=eq, band_rows=rows, tile_rows=0)
+            with lbm.lbm_batch_create(masks, taus, drhos, opts) as s:
+                assert lbm.lbm_get_launch(s)["band_rows"] == max(rows, 0)
+                lbm.lbm_step(s, 6)
+                for d, m in enumerate(masks):
+                    f = O.init(m, 1 + drhos[d], 1.0)
+                    f[~m.astype(bool)] += 1e-3 * np.random.default_rng(d).standard_normal(
+                        f[~m.astype(bool)].shape)
+                    if d % 2:
+                        lbm.lbm_set_populations(s, d, f)
+                lbm.lbm_step(s, 8)
+                obs = lbm.lbm_step_observe(s, 2)
+                runs[rows] = ([lbm.lbm_get_populations(s, d) for d in range(len(masks))], obs)
+        for rows in (1, 2, 5, 32, 64):
+            for d, (a, b) in enumerate(zip(runs[-1][0], runs[rows][0])):
+                assert np.array_equal(a, b), (eq, rows, d)
+            assert np.array_equal(runs[-1][1], runs[rows][1])
+
+
+def test_band_gather_steps_match_oracle():
+    """Band gather pairs against the FP64 oracle directly (not only through the
+    direct gather step): 10 steps from a random state on a two-piece domain
+    and a channel, TRT and BGK, within the step tolerance of the other kernels."""
+    rng = np.random.default_rng(3)
+    m1 = (rng.random((24, 530)) < 0.3).astype(np.uint8)
+    m2 = np.zeros((9, 40), np.uint8)
+    m2[0] = m2[-1] = 1
+    for coll in (0, 1):
+        opts = lbm.make_options(band_rows=8, collision=coll)
+        for m, tau in ((m1, 0.7), (m2, 1.3)):
+            f0 = O.init(m, 1.001, 1.0)
+            fl = ~m.astype(bool)
+            f0[fl] += 1e-3 * rng.standard_normal(f0[fl].shape)
+            with lbm.lbm_create_domain(m, tau, 1e-3, opts) as s:
+                assert lbm.lbm_get_launch(s)["band_rows"] == 8
+                lbm.lbm_set_populations(s, 0, f0)
+                start = lbm.lbm_get_populations(s, 0)  # FP32-rounded start
+                lbm.lbm_step(s, 10)
+                g = lbm.lbm_get_populations(s, 0)
+            tau_m = O.tau_minus(tau, 3.0 / 16.0) if coll else None
+            _assert_close(g, O.run(m, start, tau, 1.001, 1.0, 10, tau_m=tau_m), 9, m)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pair_blocks_match_whole_batch_pairs_bitwise(dim):
+    """L2-blocked pairs (the gather step of block k + 1, then the local step of
+    block k, blocks of about pair_block_mb MB cut between row groups in 2D and
+    between z planes in 3D) give the populations and observables of
+    whole-batch pairs bit for bit, from a random state, for blocks from a few
+    rows to a whole domain."""
+    rng = np.random.default_rng(40 + dim)
+    if dim == 2:
+        shapes = [(300, 600), (97, 211), (150, 1000)]
+        create, q = lbm.lbm_batch_create, 9
+    else:
+        shapes = [(40, 48, 64), (17, 23, 50)]
+        create, q = lbm.lbm_batch_create, 19
+    masks = [(rng.random(sh) < 0.3).astype(np.uint8) for sh in shapes]
+    taus = [0.55 + 0.2 * i for i in range(len(masks))]
+    drhos = [1e-3] * len(masks)
+    runs = {}
+    for mb in (-1, 1, 2, 5, 64):
+        with create(masks, taus, drhos, lbm.make_options(pair_block_mb=mb, band_rows=-1)) as s:
+            assert lbm.lbm_get_launch(s)["pair_block_mb"] == max(mb, 0)
+            for d, m in enumerate(masks):
+                f = O.init(m, 1 + drhos[d], 1.0)
+                fl = ~m.astype(bool)
+                f[fl] += 1e-3 * np.random.default_rng(d).standard_normal(f[fl].shape)
+                lbm.lbm_set_populations(s, d, f)
+            lbm.lbm_step(s, 9)
+            obs = lbm.lbm_step_observe(s, 1)
+            runs[mb] = ([lbm.lbm_get_populations(s, d) for d in range(len(masks))], obs)
+    for mb in (1, 2, 5, 64):
+        for d, (a, b) in enumerate(zip(runs[-1][0], runs[mb][0])):
+            assert np.array_equal(a, b), (dim, mb, d)
+        assert np.array_equal(runs[-1][1], runs[mb][1])
+
+
 def test_profile_steps_runs_the_same_steps_with_per_kernel_times():
     """lbm_profile_steps advances the state exactly as lbm_step does (the same
     kernels, launched one by one with events around them) and reports one
