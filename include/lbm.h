@@ -113,11 +113,12 @@ typedef struct lbm_options {
                                 (one copy per plane and row) -- ; -1 = not used; 0 = the library's default.
                                 Ignored with tile_rows > 0 (both > 0 is an error), for D3Q19 and for
                                 force-driven or slab solvers.  Bit-identical results either way. */
-    int32_t pair_block_mb;   /* in-place pairs run block by block: the gather step of block k + 1, then the local
-                                step of block k, each block about this many MB of populations, so that a block
-                                is still in L2 when its local step reads it (1..4096); -1 = whole-batch pairs;
-                                0 = the library's default.  Used with the direct gather step only.  Bit-identical
-                                results either way. */
+    int32_t pair_block_mb;   /* L2-blocked pairs (1..4096): both steps of an in-place pair in one persistent
+                                launch over blocks of about this many MB of populations -- the gather step runs
+                                about 32 MB of blocks ahead of the local step, which then reads each block
+                                while it is still in L2 -- instead of two whole-batch launches; -1 = whole-batch
+                                pairs; 0 = the library's default.  Used with the direct gather step only.
+                                Bit-identical results either way. */
 } lbm_options;
 
 /* One domain of a batch. */
@@ -414,12 +415,14 @@ lbm_status lbm_local_knudsen(lbm_handle h, int32_t d, uint32_t* d2_out, double* 
  * device time in microseconds and counts[k] the launches of each kernel kind
  * k: LBM_KERNEL_GATHER (the gather step of an in-place pair),
  * LBM_KERNEL_LOCAL (its local step), LBM_KERNEL_PULL (a pull step),
- * LBM_KERNEL_PULL_OBSERVE (unused here: always 0).  Both arrays are host
- * memory of LBM_NUM_KERNEL_KINDS entries; nsteps is at most 100000.
+ * LBM_KERNEL_PULL_OBSERVE (unused here: always 0), LBM_KERNEL_PAIR_FUSED
+ * (both steps of an L2-blocked pair in one launch, lbm_options.pair_block_mb).
+ * Both arrays are host memory of LBM_NUM_KERNEL_KINDS entries; nsteps is at
+ * most 100000.
  * No counterpart in the paper (a timing aid for the kernels of Sec. 2's step).
  */
 enum { LBM_KERNEL_GATHER = 0, LBM_KERNEL_LOCAL = 1, LBM_KERNEL_PULL = 2, LBM_KERNEL_PULL_OBSERVE = 3,
-       LBM_NUM_KERNEL_KINDS = 4 };
+       LBM_KERNEL_PAIR_FUSED = 4, LBM_NUM_KERNEL_KINDS = 5 };
 lbm_status lbm_profile_steps(lbm_handle h, int64_t nsteps, double* times_us, int64_t* counts);
 
 /*

@@ -218,15 +218,47 @@ struct GatherSmem {
     static constexpr bool on = (L::Q == 9) ? LBM_AA_GATHER_SMEM_2D : LBM_AA_GATHER_SMEM_3D;
     static constexpr int rows = (L::Q == 9) ? LBM_AA_SMEM_ROWS_2D : LBM_AA_SMEM_ROWS_3D;
 };
-template <class L, int EQ, int RS>
-__device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
+// Population loads of the step kernels: through L1 by default; CG = true
+// reads from L2 only, for a kernel whose blocks read what other blocks of the
+// same launch wrote (the fused pair below).
+template <bool CG>
+__device__ __forceinline__ float ld_pop(const float* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+template <bool CG, class T>
+__device__ __forceinline__ T ld_pop_vec(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// Population stores: plain, or (HINT) with an L2 evict-last policy so that a
+// fused pair's gather results stay in L2 until its local step rewrites them.
+#ifndef LBM_FUSED_L2HINT
+#define LBM_FUSED_L2HINT 1
+#endif
+#ifndef LBM_FUSED_LOCAL_VEC
+#define LBM_FUSED_LOCAL_VEC 2
+#endif
+template <bool HINT>
+__device__ __forceinline__ void st_pop(float* p, float v) {
+    if constexpr (HINT) {
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;\n" ::"l"(p), "f"(v), "l"(pol) : "memory");
+    } else {
+        *p = v;
+    }
+}
+
+// One strip work item of the gather step, by warp `wid` of the block (its
+// slice of the dynamic shared memory).
+template <class L, int EQ, int RS, bool CG, bool FUSED = false>
+__device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item, int wid) {
     constexpr int Q = L::Q;
     constexpr int NZ = (L::NROW == 9) ? 3 : 1;
     extern __shared__ uint32_t sme[];
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + wid;
-    if (item >= A.nitems) return;
     const uint4 it = __ldg(A.items + item);
     const uint32_t dom = it.y & 0xffffffu;
     const int nrows = (int)(it.y >> 24);
@@ -293,7 +325,7 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
                          std::make_integer_sequence<int, Q>{});
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                f[j][i] = g[chk_load(e[i], (uint32_t)Q * PS, A.err)];
+                f[j][i] = ld_pop<CG>(g + chk_load(e[i], (uint32_t)Q * PS, A.err));
                 we[(j * Q + i) * 32] = e[i];
             }
         }
@@ -304,11 +336,18 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const uint32_t e = we[(j * Q + opp<L>(i)) * 32];
-                    if (chk_store(e, (uint32_t)Q * PS, A.err)) g[e] = f[j][i];
+                    if (chk_store(e, (uint32_t)Q * PS, A.err)) st_pop<FUSED && LBM_FUSED_L2HINT>(g + e, f[j][i]);
                 }
             }
         }
     }
+}
+template <class L, int EQ, int RS>
+__device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
+    const int wid = threadIdx.x >> 5;
+    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (item >= A.nitems) return;
+    aa_gather_strip<L, EQ, RS, false>(A, item, wid);
 }
 template <class L>
 constexpr size_t gather_smem_bytes(int threads, int rs) {
@@ -980,25 +1019,29 @@ struct VecT<2> {
     __device__ static float2 join(const float (&o)[2]) { return make_float2(o[0], o[1]); }
 };
 
-template <class L, int EQ>
-__global__ void __launch_bounds__(256, LBM_AA_MINB_LOCAL) k_aa_local(const __grid_constant__ HotArgs A) {
+// One local-step work item (32 V consecutive compact slots), by one warp, in
+// passes of VV slots per lane (fewer registers for VV < V).
+template <class L, int EQ, bool CG, int VV = 4>
+__device__ __forceinline__ void aa_local_item(const HotArgs& A, uint32_t item) {
     constexpr int Q = L::Q;
-    constexpr int V = LocalVec<L>::value;
+    constexpr int VI = LocalVec<L>::value;  // slots per lane of a work item
+    constexpr int V = VV < VI ? VV : VI;    // slots per lane and pass (VI / V passes)
     using VT = VecT<V>;
     using T = typename VT::T;
     const int lane = threadIdx.x & 31;
-    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (item >= A.nvitems) return;
     const uint2 it = __ldg(A.vitems + item);
     const DomainDev D = A.dom[it.y];
     if (!D.active) return;
-    const uint32_t k = it.x + (uint32_t)lane * V;
-    if (k >= D.fluid_end) return;
     const uint32_t PS = A.pstride;
+#pragma unroll 1
+    for (int pass = 0; pass < VI / V; ++pass) {
+    const uint32_t k = it.x + (uint32_t)(pass * 32 * V) + (uint32_t)lane * V;
+    if (k >= D.fluid_end) return;
     float* const gk = A.dst[0] + k;
     float v[Q][V];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) VT::split(*reinterpret_cast<const T*>(gk + (size_t)((uint32_t)opp<L>(i) * PS)), v[i]);
+    for (int i = 0; i < Q; ++i)
+        VT::split(ld_pop_vec<CG>(reinterpret_cast<const T*>(gk + (size_t)((uint32_t)opp<L>(i) * PS))), v[i]);
     const uint32_t code = (__ldg(A.face + (k >> 4)) >> ((k & 15u) * 2u)) & ((1u << (2 * V)) - 1u);
 #pragma unroll
     for (int n = 0; n < V; ++n) {
@@ -1012,6 +1055,101 @@ __global__ void __launch_bounds__(256, LBM_AA_MINB_LOCAL) k_aa_local(const __gri
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) *reinterpret_cast<T*>(gk + (size_t)((uint32_t)i * PS)) = VT::join(v[i]);
+    }
+}
+
+template <class L, int EQ>
+__global__ void __launch_bounds__(256, LBM_AA_MINB_LOCAL) k_aa_local(const __grid_constant__ HotArgs A) {
+    const uint32_t item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= A.nvitems) return;
+    aa_local_item<L, EQ, false>(A, item);
+}
+
+// ---------------------------------------------------------------------------
+// Fused in-place pair (L2 blocking).  The batch's strip list is cut into
+// blocks of a few MB of populations (between row groups in 2D, between z
+// planes in 3D).  One persistent launch runs both steps of the pair from a
+// ticket queue of work units in the order
+//   G(0), G(1), L(0), G(2), L(1), ..., G(K-1), L(K-2), L(K-1)
+// (G(k): gather-step units of block k, L(k): local-step units of block k),
+// so a block's populations, just rewritten by its gather step, are still in
+// L2 when its local step reads them: the pair reads and writes DRAM about
+// once instead of twice.  A local unit of block k waits until every gather
+// unit of blocks k - 1, k, k + 1 is done -- the only writers of its slots --
+// on counters each gather unit increments after a fence.  Every unit it waits
+// for holds an earlier ticket and waits on nothing later, so the smallest
+// unfinished ticket always progresses: no deadlock, whatever the number of
+// resident blocks.  Blocks read populations from L2 (ld.global.cg), never
+// from a possibly stale L1 line.  A wait gives up after a bounded time, sets
+// bit 2 of the device error word and ends the block.
+// ---------------------------------------------------------------------------
+constexpr int kFusedWaitTries = 1 << 22;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <class L, int EQ, int RS>
+__device__ __forceinline__ void aa_pair_fused_body(const HotArgs& A, const PairFused& F) {
+    __shared__ uint32_t s_next;
+    __shared__ int s_ok;
+    const int wid = threadIdx.x >> 5;
+    const uint32_t W = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_next = atomicAdd(F.ctr, 1u);
+    __syncthreads();
+    uint32_t u = s_next;
+#pragma unroll 1
+    while (u < F.nunits) {
+        const uint4 U = __ldg(F.units + u);
+        __syncthreads();  // every thread has read s_next
+        if (threadIdx.x == 0) s_next = atomicAdd(F.ctr, 1u);  // the next ticket, fetched during this unit
+        const uint32_t k = U.x >> 1;
+        if ((U.x & 1u) == 0u) {
+#pragma unroll 1
+            for (uint32_t i = (uint32_t)wid; i < U.z; i += W) aa_gather_strip<L, EQ, RS, false, true>(A, U.y + i, wid);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(F.ctr + 2 + k, 1u);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                for (uint32_t b = k == 0 ? 0u : k - 1u; b <= k + 1u && b < F.nblocks && ok; ++b) {
+                    const uint32_t need = __ldg(F.total + b);
+                    int tries = 0;
+                    while (ld_acquire_u32(F.ctr + 2 + b) < need) {
+                        if (++tries > kFusedWaitTries) {
+                            ok = 0;
+                            atomicOr(A.err, 4u);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+#pragma unroll 1
+            for (uint32_t i = (uint32_t)wid; i < U.z; i += W) aa_local_item<L, EQ, true, LBM_FUSED_LOCAL_VEC>(A, U.y + i);
+        }
+        __syncthreads();  // s_next is written
+        u = s_next;
+    }
+}
+// The register caps of the gather step (the fused pair runs its code).
+template <class L, int EQ, int RS>
+__global__ void __maxnreg__(LBM_AA_GATHER_REGS_2D)
+    k_aa_pair_fused2(const __grid_constant__ HotArgs A, const __grid_constant__ PairFused F) {
+    aa_pair_fused_body<L, EQ, RS>(A, F);
+}
+template <class L, int EQ, int RS>
+__global__ void __maxnreg__(LBM_AA_GATHER_REGS_3D)
+    k_aa_pair_fused3(const __grid_constant__ HotArgs A, const __grid_constant__ PairFused F) {
+    aa_pair_fused_body<L, EQ, RS>(A, F);
 }
 
 // Face bits of the compact slots: the inlet node (x = 0) is lane 0 of a row's
@@ -1178,6 +1316,49 @@ cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, const S
     if (q == 9)
         return eq == 0 ? aa_half_launch<D2Q9, 0>(half, cfg, A, st) : aa_half_launch<D2Q9, 1>(half, cfg, A, st);
     return eq == 0 ? aa_half_launch<D3Q19, 0>(half, cfg, A, st) : aa_half_launch<D3Q19, 1>(half, cfg, A, st);
+}
+
+template <class L, int EQ>
+static cudaError_t fused_launch(const StepLaunch& cfg, const HotArgs& A, const PairFused& F, cudaStream_t st) {
+    constexpr int RS = GatherSmem<L>::rows;  // the default row batch
+    (void)cfg;
+    void (*kern)(HotArgs, PairFused);
+    if constexpr (L::Q == 9) kern = k_aa_pair_fused2<L, EQ, RS>;
+    else kern = k_aa_pair_fused3<L, EQ, RS>;
+    const size_t sm = gather_smem_bytes<L>(128, RS);
+    static std::atomic<int> grid_of[64];  // resident blocks on device d (0 = not yet known)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    int grid = grid_of[dev].load();
+    if (grid == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sm);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid = std::max(per_sm, 1) * std::max(sms, 1);
+        grid_of[dev].store(grid);
+    }
+    e = cudaMemsetAsync(F.ctr, 0, sizeof(uint32_t) * (2 + (size_t)F.nblocks), st);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)std::min<uint32_t>(F.nunits, (uint32_t)grid);
+    if (nb == 0) return cudaSuccess;
+    kern<<<nb, 128, sm, st>>>(A, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aa_pair_fused(int q, int eq, HotArgs A, const PairFused& F, float* g, const StepLaunch& cfg,
+                                 cudaStream_t st) {
+    for (int i = 0; i < 19; ++i) {
+        A.dst[i] = i < q ? g + (size_t)i * A.pstride : nullptr;
+        A.src[i] = A.dst[i];
+    }
+    if (q == 9) return eq == 0 ? fused_launch<D2Q9, 0>(cfg, A, F, st) : fused_launch<D2Q9, 1>(cfg, A, F, st);
+    return eq == 0 ? fused_launch<D3Q19, 0>(cfg, A, F, st) : fused_launch<D3Q19, 1>(cfg, A, F, st);
 }
 
 cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st) {

@@ -117,6 +117,11 @@ struct lbm_solver {
     int pair_block_mb = 0;
     std::vector<uint32_t> blk_item, blk_vitem;
     std::vector<uint4> h_items;     // host copy of the strip work list
+    // work queue of the fused pair kernel over those blocks
+    uint4* d_units = nullptr;
+    uint32_t* d_utotal = nullptr;   // gather units per block
+    uint32_t* d_uctr = nullptr;     // ticket and per-block counters
+    uint32_t nunits = 0;
     int gather_batch = 0;           // rows in flight per warp of the direct gather step (0: default)
     int strip_rows = 8;             // rows per strip work item
     std::vector<uint32_t> h_off, h_smask;  // segment offsets and fluid masks (host copies)
@@ -277,6 +282,9 @@ void free_solver(lbm_handle h) {
         dfree(h, h->d_tiles);
         dfree(h, h->d_bands);
         dfree(h, h->d_band_rng);
+        dfree(h, h->d_units);
+        dfree(h, h->d_utotal);
+        dfree(h, h->d_uctr);
         for (auto& p : h->d_col) dfree(h, p);
         dfree(h, h->d_mask);
         dfree(h, h->d_g[0]);
@@ -365,39 +373,21 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     } else if (h->opt.in_place_pairs) {
         const StepLaunch cfg = h->launch_cfg();
         const size_t K = h->blk_item.empty() ? 0 : h->blk_item.size() - 1;
-        const bool blocked = K >= 2 && cfg.tile_rows <= 0 && cfg.band_rows <= 0;
-        auto gather_of = [&](size_t k) {
-            HotArgs B = A;
-            B.items = A.items + h->blk_item[k];
-            B.nitems = h->blk_item[k + 1] - h->blk_item[k];
-            return B;
-        };
-        auto local_of = [&](size_t k) {
-            HotArgs B = A;
-            B.vitems = A.vitems + h->blk_vitem[k];
-            B.nvitems = h->blk_vitem[k + 1] - h->blk_vitem[k];
-            return B;
-        };
+        const bool blocked = K >= 2 && h->nunits > 0 && cfg.tile_rows <= 0 && cfg.band_rows <= 0;
+        PairFused F{};
+        F.units = h->d_units;
+        F.nunits = h->nunits;
+        F.nblocks = (uint32_t)K;
+        F.total = h->d_utotal;
+        F.ctr = h->d_uctr;
         for (; plain >= 2; plain -= 2) {
             if (blocked) {
-                // gather step of block k, then local step of block k - 1
-                for (size_t k = 0; k <= K; ++k) {
-                    if (k < K) {
-                        if (prof) CK(h, prof->mark(h->st));
-                        CK(h, launch_aa_half(h->q, h->eq, 0, gather_of(k), h->d_g[h->cur], cfg, h->st));
-                        if (prof) {
-                            CK(h, prof->mark(h->st));
-                            prof->kind.push_back(0);
-                        }
-                    }
-                    if (k >= 1) {
-                        if (prof) CK(h, prof->mark(h->st));
-                        CK(h, launch_aa_half(h->q, h->eq, 1, local_of(k - 1), h->d_g[h->cur], cfg, h->st));
-                        if (prof) {
-                            CK(h, prof->mark(h->st));
-                            prof->kind.push_back(1);
-                        }
-                    }
+                // both steps in one persistent launch, block by block through L2
+                if (prof) CK(h, prof->mark(h->st));
+                CK(h, launch_aa_pair_fused(h->q, h->eq, A, F, h->d_g[h->cur], cfg, h->st));
+                if (prof) {
+                    CK(h, prof->mark(h->st));
+                    prof->kind.push_back(4);
                 }
                 continue;
             }
@@ -865,6 +855,7 @@ lbm_status build_pair_blocks(lbm_handle h, int mb) {
     h->blk_item.clear();
     h->blk_vitem.clear();
     h->pair_block_mb = 0;
+    h->nunits = 0;
     if (mb <= 0 || !h->opt.in_place_pairs || h->forced || h->slab) return LBM_OK;
     const uint64_t target = std::max<uint64_t>((uint64_t)mb << 20, 1) / (4ull * (uint64_t)h->q);
     std::vector<uint32_t> cstart;  // compact index where each block begins
@@ -904,6 +895,32 @@ lbm_status build_pair_blocks(lbm_handle h, int mb) {
             while (k + 1 < K && cstart[k + 1] <= last) h->blk_vitem[++k] = j;
         }
     while (k + 1 <= K) h->blk_vitem[++k] = j;
+    // work queue: G(k) = the gather units of block k (kFusedGather strips
+    // each), L(k) = its local units (kFusedLocal items each), L(k) after
+    // G(k + lag); lag = about kFusedLagMb of blocks ahead
+    const uint32_t lag = (uint32_t)std::max(1, (kFusedLagMb + mb / 2) / mb);
+    std::vector<uint4> units;
+    std::vector<uint32_t> total(K, 0u);
+    for (size_t b = 0; b < K + lag; ++b) {
+        if (b < K)
+            for (uint32_t i = h->blk_item[b]; i < h->blk_item[b + 1]; i += kFusedGather, ++total[b])
+                units.push_back(make_uint4((uint32_t)b << 1, i, std::min(kFusedGather, h->blk_item[b + 1] - i), 0u));
+        if (b >= lag) {
+            const size_t c = b - lag;
+            for (uint32_t i = h->blk_vitem[c]; i < h->blk_vitem[c + 1]; i += kFusedLocal)
+                units.push_back(make_uint4(((uint32_t)c << 1) | 1u, i, std::min(kFusedLocal, h->blk_vitem[c + 1] - i), 0u));
+        }
+    }
+    dfree(h, h->d_units);
+    dfree(h, h->d_utotal);
+    dfree(h, h->d_uctr);
+    h->nunits = (uint32_t)units.size();
+    CK(h, dmalloc(h, &h->d_units, sizeof(uint4) * std::max<size_t>(units.size(), 1)));
+    CK(h, dmalloc(h, &h->d_utotal, sizeof(uint32_t) * K));
+    CK(h, dmalloc(h, &h->d_uctr, sizeof(uint32_t) * (K + 2)));
+    CK(h, cudaMemcpyAsync(h->d_units, units.data(), sizeof(uint4) * units.size(), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->d_utotal, total.data(), sizeof(uint32_t) * K, cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
     return LBM_OK;
 }
 

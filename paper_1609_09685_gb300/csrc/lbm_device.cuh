@@ -140,6 +140,14 @@ constexpr int kBandRowsDefault = 0;
 // is 0 (0: unblocked pairs), and the largest block size accepted.
 constexpr int kPairBlockMbDefault = 0;
 constexpr int kPairBlockMbMax = 4096;
+// Fused pair work units: strips per gather unit, local items per local unit,
+// and how far (MB of blocks) the gather step runs ahead of the local step.
+constexpr uint32_t kFusedGather = 4;
+constexpr uint32_t kFusedLocal = 16;
+#ifndef LBM_FUSED_LAG_MB
+#define LBM_FUSED_LAG_MB 32
+#endif
+constexpr int kFusedLagMb = LBM_FUSED_LAG_MB;
 
 // Arguments of the hot stream-collide kernel.
 struct HotArgs {
@@ -159,6 +167,16 @@ struct HotArgs {
     const BandItem* bands;   // band gather step: band list
     uint32_t nbands;
     const uint2* band_rng;   // band gather step: range records
+};
+
+// Work queue of the fused in-place pair (k_aa_pair_fused).
+struct PairFused {
+    const uint4* units;      // x = kind (0 gather, 1 local) | block << 1; y = first item; z = item count
+    uint32_t nunits;
+    uint32_t nblocks;
+    const uint32_t* total;   // gather units of each block
+    uint32_t* ctr;           // [0] next ticket, [1] unused, [2 + k] gather units of block k done;
+                             // zeroed before every launch
 };
 
 // Arguments shared by every segment kernel.

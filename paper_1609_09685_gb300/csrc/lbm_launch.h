@@ -21,6 +21,10 @@ struct StepLaunch {
 };
 // Two steps in place on g (gather step, then local step); see k_aa_gather.
 cudaError_t launch_aa_pair(int q, int eq, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
+// Both steps of the pair in one persistent launch over the work queue F
+// (L2-blocked; see k_aa_pair_fused); zeroes F.ctr first.
+cudaError_t launch_aa_pair_fused(int q, int eq, HotArgs A, const PairFused& F, float* g, const StepLaunch& cfg,
+                                 cudaStream_t st);
 // One half of the pair: half 0 = gather step, 1 = local step.
 cudaError_t launch_aa_half(int q, int eq, int half, HotArgs A, float* g, const StepLaunch& cfg, cudaStream_t st);
 // Nonzero when the lattice with q directions has a staged gather step.

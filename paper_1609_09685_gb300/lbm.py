@@ -472,7 +472,7 @@ def lbm_destroy(s: "Solver") -> None:
     s.close()
 
 
-KERNEL_KINDS = ("gather", "local", "pull", "pull_observe")
+KERNEL_KINDS = ("gather", "local", "pull", "pull_observe", "pair_fused")
 
 
 def lbm_profile_steps(s: Solver, nsteps: int) -> dict:

@@ -18,12 +18,15 @@ Sets (names as in the tests):
   C4  256x128x128 D3Q19, porosity 0.70, tau 0.52 and 0.6
 
     python tests/golden/make_converged_k.py [--sets C1,C2,C3] [--procs N] [--names A,B] [--maxiter M]
+    python tests/golden/make_converged_k.py --merge-only
 
-Runs one process per job (spawned), longest first.  Results are appended as
-they finish to converged_k.partial.txt and the final files are written when
-every job of the chosen sets is done (existing entries of other sets are
-kept).  Runtime on 8 x86 cores: hours (the 1200x600 and D3Q19 domains
-dominate).
+Runs one process per job (spawned), longest first.  Each result is saved as
+it finishes (a line in converged_k.partial.txt and tests/golden/partial/
+NAME.npz with the sampled velocities); when every job of the chosen sets is
+done the final files are rewritten from what they already hold plus every
+saved result, so separate runs (e.g. the 3D set alone) merge instead of
+overwriting each other.  --merge-only does just that merge.  Runtime on 8
+x86 cores: hours (the 1200x600 and D3Q19 domains dominate).
 """
 from __future__ import annotations
 
@@ -46,6 +49,7 @@ sys.path.insert(0, ROOT)
 OUT_K = os.path.join(HERE, "converged_k.txt")
 OUT_U = os.path.join(HERE, "converged_u_samples.npz")
 PARTIAL = os.path.join(HERE, "converged_k.partial.txt")
+PARTS = os.path.join(HERE, "partial")
 NSAMPLE = 256
 
 
@@ -127,33 +131,54 @@ def read_existing():
     return rows, samples
 
 
+def save_part(r):
+    os.makedirs(PARTS, exist_ok=True)
+    np.savez_compressed(os.path.join(PARTS, r["name"] + ".npz"), line=np.array(line(r)), idx=r["idx"], u=r["u"])
+
+
+def merge():
+    rows, samples = read_existing()
+    if os.path.isdir(PARTS):
+        for fn in sorted(os.listdir(PARTS)):
+            if not fn.endswith(".npz"):
+                continue
+            z = np.load(os.path.join(PARTS, fn))
+            ln = str(z["line"])
+            name = ln.split()[0]
+            rows[name] = ln
+            samples[name + "/idx"] = z["idx"]
+            samples[name + "/u"] = z["u"]
+    with open(OUT_K, "w") as fh:
+        fh.write(HEADER)
+        for name in sorted(rows):
+            fh.write(rows[name] + "\n")
+    np.savez_compressed(OUT_U, **samples)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--sets", default="C1,C2,C3")
     ap.add_argument("--procs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--names", default="", help="only these domains (comma list), e.g. to re-solve one")
     ap.add_argument("--maxiter", type=int, default=MAXITER, help="Newton iterations of the root finder")
+    ap.add_argument("--merge-only", action="store_true", help="only merge the saved results into the final files")
     a = ap.parse_args()
+    if a.merge_only:
+        merge()
+        return
     todo = sorted(jobs(set(a.sets.split(","))), key=lambda j: -cost(j[2]))
     if a.names:
         keep = set(a.names.split(","))
         todo = [j for j in todo if j[1] in keep]
     todo = [j + (a.maxiter,) for j in todo]
-    rows, samples = read_existing()
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as part:
         for r in pool.imap_unordered(solve, todo):
-            rows[r["name"]] = line(r)
-            samples[r["name"] + "/idx"] = r["idx"]
-            samples[r["name"] + "/u"] = r["u"]
+            save_part(r)
             part.write(line(r) + f"  # {r['seconds']:.0f} s converged={r['converged']}\n")
             part.flush()
             print(line(r), f"{r['seconds']:.0f} s", flush=True)
-    with open(OUT_K, "w") as fh:
-        fh.write(HEADER)
-        for name in sorted(rows):
-            fh.write(rows[name] + "\n")
-    np.savez_compressed(OUT_U, **samples)
+    merge()
 
 
 if __name__ == "__main__":

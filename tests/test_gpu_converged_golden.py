@@ -15,6 +15,12 @@ stall stops).  The target: k within 1e-4 relative of the oracle's, and the
 velocity within 1e-3 relative L2 over the stored sample of fluid nodes (256
 per domain, drawn once by the generator).  A set without stored values is
 skipped.
+
+Only oracle states at the fixed point to the rounding level of the FP64 step
+are used: max-norm residual |S(f) - f| <= 1e-13 (plain FP64 iteration stalls
+near 1e-14 on these domains).  A stored row above that -- the root finder hit
+its iteration cap on a slowly converging domain -- is left out, and the test
+names it.
 """
 import os
 
@@ -26,6 +32,7 @@ from paper_1609_09685_gb300 import build, lbm
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+RESIDUAL_MAX = 1e-13
 GOLD_K = os.path.join(HERE, "golden", "converged_k.txt")
 GOLD_U = os.path.join(HERE, "golden", "converged_u_samples.npz")
 
@@ -36,7 +43,7 @@ def _lib():
     lbm.load()
 
 
-def _rows(set_name):
+def _rows(set_name, excluded=None):
     rows = []
     if not os.path.exists(GOLD_K):
         return rows
@@ -46,18 +53,27 @@ def _rows(set_name):
         t = line.split()
         if not t[0].startswith(set_name + "_"):
             continue
-        rows.append(dict(name=t[0], nx=int(t[1]), ny=int(t[2]), nz=int(t[3]), seed=int(t[4]), porosity=float(t[5]),
-                         tau=float(t[6]), drho=float(t[7]), k=float(t[8]), residual=float(t[9]),
-                         percolates=bool(int(t[11]))))
+        r = dict(name=t[0], nx=int(t[1]), ny=int(t[2]), nz=int(t[3]), seed=int(t[4]), porosity=float(t[5]),
+                 tau=float(t[6]), drho=float(t[7]), k=float(t[8]), residual=float(t[9]), percolates=bool(int(t[11])))
+        if r["residual"] <= RESIDUAL_MAX:
+            rows.append(r)
+        elif excluded is not None:
+            excluded.append((r["name"], r["residual"]))
     return rows
 
 
 @pytest.mark.parametrize("set_name", ["C1", "C2", "C3", "C4"])
 def test_converged_permeability_and_velocity_match_the_oracle(set_name):
-    rows = _rows(set_name)
+    excluded = []
+    rows = _rows(set_name, excluded)
+    if excluded:
+        print(f"{set_name}: oracle states above the residual bound, left out: {excluded}")
     if not rows:
-        pytest.skip(f"no stored oracle values for {set_name}")
+        pytest.skip(f"no stored oracle values for {set_name} within the residual bound (left out: {excluded})")
     samples = np.load(GOLD_U)
+    rows = [r for r in rows if r["name"] + "/idx" in samples.files]
+    if not rows:
+        pytest.skip(f"no stored velocity samples for {set_name}")
     masks = []
     for r in rows:
         shape = (r["ny"], r["nx"]) if r["nz"] == 1 else (r["nz"], r["ny"], r["nx"])
