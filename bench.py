@@ -84,6 +84,11 @@ def parse():
     p.add_argument("--ws-eval", type=int, default=16, help="held-out evaluation domains")
     p.add_argument("--ws-epochs", type=int, default=30)
     p.add_argument("--ws-shape", default="256x512", help="ny x nx of the warm-start domains")
+    p.add_argument("--ws-weights", default="",
+                   help="extra loss weights (density, u_x, u_y) to train and evaluate as well, ';'-separated")
+    p.add_argument("--ws-ablations", action="store_true",
+                   help="also warm-start from the converged density, velocity or both (diagnosis)")
+    p.add_argument("--ws-plain", type=int, default=32, help="held-out domains also solved one at a time")
     return p.parse_args()
 
 
@@ -336,13 +341,13 @@ def measure_warmstart(args, lbm, sp):
     t0 = time.perf_counter()
     hist = WS.train(net, ds, epochs=args.ws_epochs, batch=8, lr=2e-3)
     t_train = time.perf_counter() - t0
-    res = WS.evaluate(net, ev)
-    # plain: one domain at a time from the equilibrium start, on the domains
-    # that converged in both batched runs
+    res = WS.evaluate(net, ev, ablations=args.ws_ablations)
+    # plain: one domain at a time from the equilibrium start, on (a sample of
+    # at most --ws-plain of) the domains that converged in both batched runs
     eq, wm = res["equilibrium"], res["warm"]
     both = [d for d in range(len(ev)) if eq["per_domain"][d]["status"] == 0 and wm["per_domain"][d]["status"] == 0]
     plain_t, plain_steps = [], []
-    for d in both:
+    for d in both[:args.ws_plain]:
         s1 = lbm.lbm_create_domain(ev.masks_host[d], ev.taus[d], ev.drhos[d], lbm.make_options())
         lbm.lbm_run_to_steady(s1, 1e-9, 400_000)
         stp, kk, rr, tt = lbm.lbm_get_history(s1, 0)
@@ -352,8 +357,23 @@ def measure_warmstart(args, lbm, sp):
             continue
         plain_t.append(tk)
         plain_steps.append(int(stp[ik]))
+    extra = []
+    for wspec in [w for w in args.ws_weights.split(";") if w.strip()]:
+        wts = tuple(float(v) for v in wspec.split(","))
+        net2 = WS.UNet(chans, seed=0)
+        t0 = time.perf_counter()
+        h2 = WS.train(net2, ds, epochs=args.ws_epochs, batch=8, lr=2e-3, weights=wts)
+        t2 = time.perf_counter() - t0
+        r2 = WS.evaluate(net2, ev)
+        extra.append({"loss_weights": list(wts), "train_s": t2, "loss_first_last": [h2[0], h2[-1]],
+                      "domains_compared": r2["domains_converged_both"],
+                      "batched_steps_to_k": r2["steps_to_k_equilibrium"],
+                      "batched_warm_steps_to_k": r2["steps_to_k_warm"],
+                      "batched_time_to_k_s": r2["time_to_all_k_equilibrium_s"],
+                      "batched_warm_time_to_k_s": r2["time_to_all_k_warm_s"]})
     return {
-        "shape": [ny, nx], "domains_compared": len(both), "domains_not_converged": res["domains_not_converged"], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
+        "shape": [ny, nx], "domains_compared": len(both), "loss_weights": list(WS.LOSS_WEIGHTS),
+        "other_loss_weights": extra, "domains_not_converged": res["domains_not_converged"], "train_solutions": len(ds), "eval_domains": len(ev), "unet_levels": levels,
         "unet_params": int(net.nparams), "epochs": args.ws_epochs, "loss_first_last": [hist[0], hist[-1]],
         "datagen_s": t_gen, "train_s": t_train, "tol_rel": args.ttp_tol,
         "plain_time_to_k_s": float(sum(plain_t)), "plain_steps_to_k": int(sum(plain_steps)),
@@ -362,8 +382,11 @@ def measure_warmstart(args, lbm, sp):
         "batched_steps_to_k": res["steps_to_k_equilibrium"], "batched_warm_steps_to_k": res["steps_to_k_warm"],
         "warm_predict_s": wm["predict_s"], "k_rel_diff_warm_vs_equilibrium_max": res["k_rel_diff_max"],
         "k_rel_diff_warm_vs_equilibrium": res["k_rel_diff"],
+        "plain_domains": min(len(both), args.ws_plain),
         "per_domain_steps_to_k": {"equilibrium": [eq["per_domain"][d]["steps_to_k"] for d in both],
                                   "warm": [wm["per_domain"][d]["steps_to_k"] for d in both]},
+        "ablations": {k: v for k, v in res.items() if k.startswith(("steps_to_k_warm_true", "steps_to_k_equilibrium_on",
+                                                                    "domains_warm_true"))},
     }
 
 

@@ -340,21 +340,43 @@ def time_to_k(t, k, tol, k_ref=None):
     return float(t[i]), i
 
 
+# Ablations of the warm start: the converged fields' channels put in place of
+# the network's (0 = density deviation, 1, 2 = velocity), to see which part of
+# the prediction limits the gain.
+ABLATIONS = {"warm_true_density": (0,), "warm_true_velocity": (1, 2), "warm_true_fields": (0, 1, 2)}
+
+
+def _with_true_channels(y, ds: Dataset, i0: int, nb: int, chans, stream=None):
+    """Copy the stored targets' channels `chans` of domains i0 .. i0 + nb - 1
+    into the prediction y (bf16 [nb, h, w, C_OUT]), with the library's kernels."""
+    torch = _torch()
+    tb = torch.empty((nb, ds.h, ds.w, N_TARGET), dtype=torch.bfloat16, device="cuda")
+    lbm.lbm_nn_f32_to_bf16(ds.targets[i0:i0 + nb], tb, tb.numel(), stream)
+    for c in chans:
+        lbm.lbm_nn_copy_channels(tb, N_TARGET, c, y, C_OUT, c, 1, nb * ds.h * ds.w, stream)
+    return y
+
+
 def evaluate(net: UNet, ds: Dataset, stream=None, tol_k: float = 1e-4, max_steps: int = 400_000,
-             tol: float = 1e-9, batch: int = 8):
+             tol: float = 1e-9, batch: int = 8, ablations: bool = False):
     """Equilibrium start vs warm start on the same domains (one batched solver
     each); returns per-domain steps and times to k within tol_k of each run's
-    converged k, and the converged k of both."""
+    converged k, and the converged k of both.  With ablations, also warm
+    starts whose density, velocity or both come from the converged solution
+    (the targets) instead of the network."""
     torch = _torch()
     n = len(ds)
     res = {}
-    for mode in ("equilibrium", "warm"):
+    modes = ["equilibrium", "warm"] + (list(ABLATIONS) if ablations else [])
+    for mode in modes:
         s = lbm.lbm_batch_create(ds.masks_host, ds.taus, ds.drhos, lbm.make_options(stream=stream))
         t0 = time.perf_counter()
-        if mode == "warm":
+        if mode != "equilibrium":
             for i0 in range(0, n, batch):
                 nb = min(batch, n - i0)
                 y = predict(net, ds, i0, nb)
+                if mode in ABLATIONS:
+                    y = _with_true_channels(y, ds, i0, nb, ABLATIONS[mode], stream)
                 for d in range(nb):
                     lbm.lbm_warm_start(s, i0 + d, y[d], C_OUT)
             torch.cuda.synchronize()
@@ -384,4 +406,10 @@ def evaluate(net: UNet, ds: Dataset, stream=None, tol_k: float = 1e-4, max_steps
     res["steps_to_k_warm"] = int(np.sum([wm["per_domain"][d]["steps_to_k"] for d in both]))
     res["time_to_all_k_equilibrium_s"] = max([eq["per_domain"][d]["time_to_k"] for d in both], default=None)
     res["time_to_all_k_warm_s"] = max([wm["per_domain"][d]["time_to_k"] for d in both], default=None)
+    for mode in ABLATIONS:
+        if mode in res:
+            ok = [d for d in both if res[mode]["per_domain"][d]["steps_to_k"] is not None]
+            res["steps_to_k_" + mode] = int(np.sum([res[mode]["per_domain"][d]["steps_to_k"] for d in ok]))
+            res["steps_to_k_equilibrium_on_" + mode] = int(np.sum([eq["per_domain"][d]["steps_to_k"] for d in ok]))
+            res["domains_" + mode] = len(ok)
     return res
