@@ -458,6 +458,26 @@ def measure_forced3d(lbm, sp):
         out[name] = {"k": [float(v) for v in k], "k_over_k_smallest_g": [float(v / k[0]) for v in k],
                      "status": [int(v) for v in st], "steps": [int(v) for v in steps], "seconds": dt,
                      "mlups": float(sum(int(v) for v in steps) * int((mask == 0).sum()) / dt / 1e6)}
+        if name == "quadratic":
+            # per-kernel device time of the plain steps (forced gather and local
+            # steps of the in-place pairs, one pull step), CUDA events per launch
+            s2 = lbm.lbm_batch_create_forced([mask] * 3, [tau] * 3, gs, lbm.make_options(stream=sp, equilibrium=eq))
+            lbm.lbm_step(s2, 100)
+            prof = lbm.lbm_profile_steps(s2, 101)
+            s2.close()
+            fluid = 3 * int((mask == 0).sum())
+            bpl = 2 * 4 * 19 * fluid
+            peak, peak_src = measured_hbm_peak()
+            kern = {}
+            for kind in ("gather", "local", "pull"):
+                t_us, n = prof[kind]
+                if n:
+                    us = t_us / n
+                    kern[kind] = {"avg_launch_us": us, "launches": n, "achieved": bpl / us / 1e3,
+                                  "frac": bpl / us / 1e3 / peak}
+            out["kernels"] = {"domains": 3, "fluid_nodes": fluid, "bytes_per_launch": bpl,
+                              "algorithmic_bytes": "152 B per fluid-node update (one step)", "peak": peak,
+                              "peak_source": peak_src, "per_kind": kern}
         s.close()
     return out
 

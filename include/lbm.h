@@ -220,8 +220,11 @@ lbm_status lbm_batch_create(int32_t n, const lbm_domain_desc* descs, const lbm_o
  * lbm_permeability then returns Eq. 2's k = nu <u>/g, <u> the sum over fluid
  * nodes of rho u_x over rho_out N_grid, with rho u the fluid momentum of Guo's
  * scheme (the pre-collision momentum plus F/2, i.e. the stored post-collision
- * momentum minus F/2).  BGK or TRT (opt->collision); steps are pull steps of a
- * kernel of their own (opt->in_place_pairs is ignored).
+ * momentum minus F/2).  BGK or TRT (opt->collision).  Plain steps run as
+ * in-place pairs of kernels of their own (a forced gather step that writes
+ * each result back to the slot it read, then a forced step on each node's own
+ * slots) when opt->in_place_pairs is 1 (the default), else as pull steps; the
+ * two give bit-identical populations.
  * lbm_save, lbm_nn_targets and lbm_warm_start return LBM_ERR_ARG on such a
  * solver.
  */
@@ -336,8 +339,8 @@ lbm_status lbm_time_steps(lbm_handle h, int32_t nsteps, double* us_per_step);
  * gather step with 16, 32 and 64 band rows.  With
  * cache_path (nullable), the choice is looked up first under the key of
  * lbm_tune_key and stored after a search.  Force-driven solvers have nothing
- * to tune (their steps are pull steps of their own kernel): the call only
- * reports their configuration.  out (nullable) receives the chosen and the
+ * to tune (their steps run kernels of their own in one fixed configuration):
+ * the call only reports their configuration.  out (nullable) receives the chosen and the
  * default configuration with their times per plain step, the number of
  * configurations timed (0 when the cache answered) and whether it did.
  */

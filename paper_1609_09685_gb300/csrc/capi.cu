@@ -358,7 +358,21 @@ lbm_status enqueue_steps(lbm_handle h, int64_t n, bool obs, KernelProf* prof = n
     const int64_t o = (obs && n > 0) ? 1 : 0;
     int64_t plain = n - o;
     if (h->forced) {
-        for (int64_t k = 0; k < n; ++k) {
+        // plain steps two at a time in place (forced gather step + local
+        // step), the rest as pull steps
+        int64_t k0 = 0;
+        if (h->opt.in_place_pairs) {
+            for (; plain >= 2; plain -= 2, k0 += 2)
+                for (int half = 0; half < 2; ++half) {
+                    if (prof) CK(h, prof->mark(h->st));
+                    CK(h, launch_periodic_half(h->q, h->eq, half, A, h->d_gforce, h->d_g[h->cur], h->st));
+                    if (prof) {
+                        CK(h, prof->mark(h->st));
+                        prof->kind.push_back(half);
+                    }
+                }
+        }
+        for (int64_t k = k0; k < n; ++k) {
             const bool ob = (o == 1) && (k == n - 1);
             if (prof) CK(h, prof->mark(h->st));
             CK(h, launch_periodic_step(h->q, h->eq, ob, A, h->d_gforce, h->d_g[h->cur], h->d_g[h->cur ^ 1],
@@ -979,7 +993,6 @@ static lbm_status create_impl(int32_t n, const lbm_domain_desc* descs, const lbm
         return fail(nullptr, LBM_ERR_ARG, "invalid options");
     if (slab) o.in_place_pairs = 0;  // a slab's ghost columns are refreshed between single pull steps
     if (gforce) {
-        o.in_place_pairs = 0;  // force-driven steps are pull steps of their own kernel
         for (int d = 0; d < n; ++d)
             if (!std::isfinite(gforce[d])) return fail(nullptr, LBM_ERR_ARG, "g must be finite");
     }

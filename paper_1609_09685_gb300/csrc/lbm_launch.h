@@ -89,6 +89,9 @@ int qsgs_generate(uint64_t seed, int nx, int ny, int nz, double core_p, double p
 // observing when obs; gforce = body acceleration per domain (device).
 cudaError_t launch_periodic_step(int q, int eq, bool obs, HotArgs A, const float* gforce, const float* src,
                                  float* dst, float* uprev, double* partials, cudaStream_t st);
+// One half of a force-driven in-place pair on g: half 0 = gather step (pull
+// reads, results written back to the slots read), 1 = local step.
+cudaError_t launch_periodic_half(int q, int eq, int half, HotArgs A, const float* gforce, float* g, cudaStream_t st);
 
 // Local pore size (pore.cu): exact squared distance to the nearest solid node of
 // a dense mask (d2, tmp: nx*ny*nz uint32 each), then h = 2 D - 1 and the local Kn.

@@ -23,6 +23,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
+#include "lbm_stencil.cuh"
 
 namespace lbmgb {
 
@@ -43,31 +44,99 @@ __device__ __forceinline__ PWin pwin(const uint4 r, int lane, uint32_t lmask) {
     return w;
 }
 
-template <class L>
-__device__ __forceinline__ void pmoments(const float (&f)[L::Q], float& dr, float& jx, float& jy, float& jz) {
-    dr = jx = jy = jz = 0.f;
+// Forced BGK / TRT collision of one node (Guo forcing, see above), every
+// floating-point operation written out (fmaf or the __f*_rn intrinsics, never
+// fused by the compiler), so that the pull step, the gather step and the
+// local step relax a node to the same bits.  f: pre-collision on entry,
+// post-collision on return; dr, jx, jy, jz: the node's density deviation and
+// pre-collision momentum, irho = 1 / rho (for the observables).
+template <class L, int EQ>
+__device__ __forceinline__ void forced_relax(float (&f)[L::Q], float rho0, float F, float om, float omm, float& dr,
+                                             float& jx, float& jy, float& jz, float& irho) {
+    constexpr int Q = L::Q;
+    moments<L>(f, dr, jx, jy, jz);
+    irho = __fdividef(1.0f, __fadd_rn(rho0, dr));
+    const float jsx = fmaf(0.5f, F, jx);  // equilibrium momentum j' = j + F/2
+    const float ux = __fmul_rn(jsx, irho), uy = __fmul_rn(jy, irho), uz = __fmul_rn(jz, irho);
+    const float jj = (L::D == 3) ? fmaf(jsx, jsx, fmaf(jy, jy, __fmul_rn(jz, jz))) : fmaf(jsx, jsx, __fmul_rn(jy, jy));
+    const float omc = __fsub_rn(1.0f, om), hf = __fsub_rn(1.0f, __fmul_rn(0.5f, om));
+    const float hfm = __fsub_rn(1.0f, __fmul_rn(0.5f, omm));
+    const bool trt = (omm != om);
+    const float uF = __fmul_rn(ux, F);
+    auto eqs = [&](int i, float& eqi, float& Si) {
+        const float wi = (float)L::wd(i);
+        const float cj = cdot<L>(i, jsx, jy, jz);
+        const float cF = L::c(i, 0) > 0 ? F : (L::c(i, 0) < 0 ? -F : 0.f);
+        if (EQ == 0) {
+            const float quad = fmaf(4.5f, __fmul_rn(cj, cj), __fmul_rn(-1.5f, jj));
+            eqi = __fmul_rn(wi, fmaf(irho, quad, fmaf(3.0f, cj, dr)));
+            const float cu = cdot<L>(i, ux, uy, uz);
+            Si = __fmul_rn(wi, fmaf(9.0f, __fmul_rn(cu, cF), __fmul_rn(3.0f, __fsub_rn(cF, uF))));
+        } else {
+            eqi = __fmul_rn(wi, fmaf(3.0f, cj, dr));
+            Si = __fmul_rn(3.0f, __fmul_rn(wi, cF));
+        }
+    };
+    float dsum = 0.f;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        dr += f[i];
-        if (L::c(i, 0) > 0) jx += f[i];
-        if (L::c(i, 0) < 0) jx -= f[i];
-        if (L::c(i, 1) > 0) jy += f[i];
-        if (L::c(i, 1) < 0) jy -= f[i];
-        if (L::c(i, 2) > 0) jz += f[i];
-        if (L::c(i, 2) < 0) jz -= f[i];
+    for (int i = 1; i < Q; ++i) {
+        if (opp<L>(i) < i) continue;
+        const int o = opp<L>(i);
+        float ei, si, eo, so;
+        eqs(i, ei, si);
+        eqs(o, eo, so);
+        const float fi = f[i], fo = f[o];
+        float oi, oo;
+        if (!trt) {
+            oi = fmaf(omc, fi, fmaf(om, ei, __fmul_rn(hf, si)));
+            oo = fmaf(omc, fo, fmaf(om, eo, __fmul_rn(hf, so)));
+        } else {
+            const float fp = __fmul_rn(0.5f, __fadd_rn(fi, fo)), fm = __fmul_rn(0.5f, __fsub_rn(fi, fo));
+            const float ep = __fmul_rn(0.5f, __fadd_rn(ei, eo)), em = __fmul_rn(0.5f, __fsub_rn(ei, eo));
+            const float sp = __fmul_rn(0.5f, __fadd_rn(si, so)), sm = __fmul_rn(0.5f, __fsub_rn(si, so));
+            const float even = fmaf(hf, sp, __fmul_rn(-om, __fsub_rn(fp, ep)));
+            const float odd = fmaf(hfm, sm, __fmul_rn(-omm, __fsub_rn(fm, em)));
+            oi = __fadd_rn(fi, __fadd_rn(even, odd));
+            oo = __fadd_rn(fo, __fsub_rn(even, odd));
+        }
+        dsum = pair_dsum(dsum, fi, fo, oi, oo);
+        f[i] = oi;
+        f[o] = oo;
     }
+    f[0] = __fadd_rn(f[0], dsum);  // mass balance
 }
 
-template <class L>
-__device__ __forceinline__ float pdot(int i, float vx, float vy, float vz) {
-    float r = 0.f;
-    if (L::c(i, 0) > 0) r += vx;
-    if (L::c(i, 0) < 0) r -= vx;
-    if (L::c(i, 1) > 0) r += vy;
-    if (L::c(i, 1) < 0) r -= vy;
-    if (L::c(i, 2) > 0) r += vz;
-    if (L::c(i, 2) < 0) r -= vz;
-    return r;
+// Source of direction i for the lane's node (periodic pull streaming): the
+// global element of the fluid source, or of the node's own opposite slot
+// (bounce-back from a solid source; a solid lane's kd is the next fluid slot,
+// at most the padding slot).
+template <class L, int I>
+__device__ __forceinline__ uint32_t psrc(const PWin (&w)[L::NROW], const uint32_t (&fl_l)[L::NROW],
+                                         const uint32_t (&ix_l)[L::NROW], const uint32_t (&fl_r)[L::NROW],
+                                         const uint32_t (&ix_r)[L::NROW], bool wrapl, bool wrapr, uint32_t kd,
+                                         uint32_t PS) {
+    constexpr int cx = L::c(I, 0);
+    constexpr int q = (1 - L::c(I, 1)) + (L::NROW == 9 ? 3 * (1 - L::c(I, 2)) : 0);  // source row
+    bool sf;
+    uint32_t idx;
+    if (cx == 0) {
+        sf = (w[q].tri >> 1) & 1u;
+        idx = w[q].i0 + (w[q].tri & 1u);
+    } else if (cx > 0) {  // source x - 1
+        sf = wrapl ? (fl_l[q] != 0u) : ((w[q].tri & 1u) != 0u);
+        idx = wrapl ? ix_l[q] : w[q].i0;
+    } else {  // source x + 1
+        sf = wrapr ? (fl_r[q] != 0u) : (((w[q].tri >> 2) & 1u) != 0u);
+        idx = wrapr ? ix_r[q] : w[q].i0 + (w[q].tri & 1u) + ((w[q].tri >> 1) & 1u);
+    }
+    return sf ? (uint32_t)I * PS + idx : (uint32_t)opp<L>(I) * PS + kd;
+}
+template <class L, int... Is>
+__device__ __forceinline__ void psrcs(uint32_t (&e)[L::Q], const PWin (&w)[L::NROW], const uint32_t (&fl_l)[L::NROW],
+                                      const uint32_t (&ix_l)[L::NROW], const uint32_t (&fl_r)[L::NROW],
+                                      const uint32_t (&ix_r)[L::NROW], bool wrapl, bool wrapr, uint32_t kd,
+                                      uint32_t PS, std::integer_sequence<int, Is...>) {
+    ((e[Is] = psrc<L, Is>(w, fl_l, ix_l, fl_r, ix_r, wrapl, wrapr, kd, PS)), ...);
 }
 
 __device__ __forceinline__ float pwarp_sum(float v) {
@@ -83,11 +152,47 @@ __device__ __forceinline__ float pwarp_max(float v) {
 
 }  // namespace
 
-template <class L, int EQ, bool OBS>
-__global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ HotArgs A, const float* __restrict__ gforce,
-                                                      float* __restrict__ uprev, double* __restrict__ partials) {
-    constexpr int Q = L::Q;
+// Neighbour windows of row (y, z) for the lane: the windows of the source rows
+// (rows and planes wrap) and, for the lanes at x = 0 and x = N_x - 1, the fluid
+// flag and compact slot of their x neighbour at the other end of each source
+// row (from that row's end segment).
+template <class L>
+struct PRow {
+    PWin w[L::NROW];
+    uint32_t fl_l[L::NROW], ix_l[L::NROW], fl_r[L::NROW], ix_r[L::NROW];
+};
+template <class L>
+__device__ __forceinline__ void prow(PRow<L>& R, const SegWindow* wdom, int y, int z, int s, int ny, int nz,
+                                     int nseg, int lastl, bool wrapl, bool wrapr, int lane, uint32_t lmask) {
     constexpr int NZ = (L::NROW == 9) ? 3 : 1;
+    auto rec = [&](int zz, int yy, int ss) { return __ldg(wdom + ((uint32_t)zz * ny + (uint32_t)yy) * nseg + ss); };
+#pragma unroll
+    for (int q = 0; q < L::NROW; ++q) {
+        const int dy = q % 3 - 1, dz = (NZ == 3) ? q / 3 - 1 : 0;
+        const int yy = (y + dy + ny) % ny, zz = (z + dz + nz) % nz;
+        R.w[q] = pwin(rec(zz, yy, s), lane, lmask);
+        R.fl_l[q] = R.ix_l[q] = R.fl_r[q] = R.ix_r[q] = 0u;
+        if (wrapl) {  // node N_x - 1 of the source row: lane lastl of its last segment
+            const uint4 e = rec(zz, yy, nseg - 1);
+            R.fl_l[q] = (e.w >> lastl) & 1u;
+            R.ix_l[q] = e.z + (e.x & 1u) + __popc(e.w & ((1u << lastl) - 1u));
+        }
+        if (wrapr) {  // node 0 of the source row: lane 0 of its first segment
+            const uint4 e = rec(zz, yy, 0);
+            R.fl_r[q] = e.w & 1u;
+            R.ix_r[q] = e.z + (e.x & 1u);
+        }
+    }
+}
+
+// Pull step (OBS: the observing variant) and the gather step of an in-place
+// pair (GATHER: each result written back to the slot it was read from, the
+// rule of the pressure-driven pair; periodic streaming and bounce-back keep
+// the pairing exact).
+template <class L, int EQ, bool OBS, bool GATHER>
+__device__ __forceinline__ void periodic_strip(const HotArgs& A, const float* __restrict__ gforce,
+                                               float* __restrict__ uprev, double* __restrict__ partials) {
+    constexpr int Q = L::Q;
     const int lane = threadIdx.x & 31;
     const uint32_t item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (item >= A.nitems) return;
@@ -101,124 +206,52 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
     }
     const int y0 = (int)(it.z & 0xffffu), z = (int)(it.z >> 16);
     const int s = (int)it.w;
-    const int x = s * kSegW + lane;
     const uint32_t lmask = (1u << lane) - 1u;
     const uint32_t PS = A.pstride;
     const int ny = D.ny, nz = D.nz, nseg = D.nseg;
     const int lastl = (D.nx - 1) & 31;
-    const bool wrapl = (s == 0 && lane == 0);                     // x = 0: its x - 1 is N_x - 1
-    const bool wrapr = (s == nseg - 1 && lane == lastl);          // x = N_x - 1: its x + 1 is 0
-    const float om = D.omega, omc = 1.0f - om, hf = 1.0f - 0.5f * om;
-    const float omm = D.omega_m, hfm = 1.0f - 0.5f * omm;
-    const bool trt = (omm != om);
-    const float F = gforce[dom] * D.rho0;
+    const bool wrapl = (s == 0 && lane == 0);             // x = 0: its x - 1 is N_x - 1
+    const bool wrapr = (s == nseg - 1 && lane == lastl);  // x = N_x - 1: its x + 1 is 0
+    const float om = D.omega, omm = D.omega_m;
+    const float F = __fmul_rn(gforce[dom], D.rho0);
     const float* src = A.src[0];
     float* const dst0 = A.dst[0];
     const SegWindow* wdom = A.win + D.seg_base;
-    auto rec = [&](int zz, int yy, int ss) { return __ldg(wdom + ((uint32_t)zz * ny + (uint32_t)yy) * nseg + ss); };
     float a0s = 0.f, a1s = 0.f, a2s = 0.f, a5s = 0.f, a6s = 0.f, umax2 = 0.f;
     int nbad = 0;
 #pragma unroll 1
     for (int r = 0; r < nrows; ++r) {
         const int y = y0 + r;
-        PWin w[L::NROW];
-        uint32_t fl_l[L::NROW], ix_l[L::NROW], fl_r[L::NROW], ix_r[L::NROW];
-#pragma unroll
-        for (int q = 0; q < L::NROW; ++q) {
-            const int dy = q % 3 - 1, dz = (NZ == 3) ? q / 3 - 1 : 0;
-            const int yy = (y + dy + ny) % ny, zz = (z + dz + nz) % nz;
-            w[q] = pwin(rec(zz, yy, s), lane, lmask);
-            fl_l[q] = ix_l[q] = fl_r[q] = ix_r[q] = 0u;
-            if (wrapl) {  // node N_x - 1 of the source row: lane lastl of its last segment
-                const uint4 e = rec(zz, yy, nseg - 1);
-                fl_l[q] = (e.w >> lastl) & 1u;
-                ix_l[q] = e.z + (e.x & 1u) + __popc(e.w & ((1u << lastl) - 1u));
-            }
-            if (wrapr) {  // node 0 of the source row: lane 0 of its first segment
-                const uint4 e = rec(zz, yy, 0);
-                fl_r[q] = e.w & 1u;
-                ix_r[q] = e.z + (e.x & 1u);
-            }
-        }
+        PRow<L> R;
+        prow<L>(R, wdom, y, z, s, ny, nz, nseg, lastl, wrapl, wrapr, lane, lmask);
         constexpr int C = (L::NROW == 9) ? 4 : 1;
-        const bool fl = (w[C].tri >> 1) & 1u;
-        const uint32_t kd = w[C].i0 + (w[C].tri & 1u);
+        const bool fl = (R.w[C].tri >> 1) & 1u;
+        const uint32_t kd = R.w[C].i0 + (R.w[C].tri & 1u);
+        uint32_t e[Q];
+        psrcs<L>(e, R.w, R.fl_l, R.ix_l, R.fl_r, R.ix_r, wrapl, wrapr, kd, PS, std::make_integer_sequence<int, Q>{});
         float f[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::c(i, 0);
-            const int q = (1 - L::c(i, 1)) + (L::NROW == 9 ? 3 * (1 - L::c(i, 2)) : 0);  // source row
-            bool sf;
-            uint32_t idx;
-            if (cx == 0) {
-                sf = (w[q].tri >> 1) & 1u;
-                idx = w[q].i0 + (w[q].tri & 1u);
-            } else if (cx > 0) {  // source x - 1
-                sf = wrapl ? (fl_l[q] != 0u) : ((w[q].tri & 1u) != 0u);
-                idx = wrapl ? ix_l[q] : w[q].i0;
-            } else {  // source x + 1
-                sf = wrapr ? (fl_r[q] != 0u) : (((w[q].tri >> 2) & 1u) != 0u);
-                idx = wrapr ? ix_r[q] : w[q].i0 + (w[q].tri & 1u) + ((w[q].tri >> 1) & 1u);
-            }
-            // solid source: halfway bounce-back from the node's own opposite slot;
-            // a solid lane's kd is the next fluid slot (at most the padding slot)
-            f[i] = sf ? src[(uint32_t)i * PS + idx] : src[(uint32_t)opp<L>(i) * PS + kd];
-        }
+        for (int i = 0; i < Q; ++i) f[i] = src[e[i]];
         if (!fl) continue;
-        float dr, jx, jy, jz;
-        pmoments<L>(f, dr, jx, jy, jz);
-        const float rho = D.rho0 + dr;
-        const float irho = __fdividef(1.0f, rho);
-        const float jsx = jx + 0.5f * F;  // equilibrium momentum j' = j + F/2
-        const float ux = jsx * irho, uy = jy * irho, uz = jz * irho;
-        const float jj = jsx * jsx + jy * jy + jz * jz;
-        float dsum = 0.f;
-        float* const dk = dst0 + kd;
-        auto eqs = [&](int i, float& eqi, float& Si) {
-            const float wi = (float)L::wd(i);
-            const float cj = pdot<L>(i, jsx, jy, jz);
-            const float cF = (float)L::c(i, 0) * F;
-            if (EQ == 0) {
-                eqi = wi * (dr + 3.0f * cj + irho * (4.5f * cj * cj - 1.5f * jj));
-                const float cu = pdot<L>(i, ux, uy, uz);
-                Si = wi * (3.0f * (cF - ux * F) + 9.0f * cu * cF);
-            } else {
-                eqi = wi * (dr + 3.0f * cj);
-                Si = 3.0f * wi * cF;
-            }
-        };
+        float dr, jx, jy, jz, irho;
+        forced_relax<L, EQ>(f, D.rho0, F, om, omm, dr, jx, jy, jz, irho);
+        if (GATHER) {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (opp<L>(i) < i) continue;
-            const int o = opp<L>(i);
-            float ei, si, eo, so;
-            eqs(i, ei, si);
-            eqs(o, eo, so);
-            float oi, oo;
-            if (!trt) {
-                oi = fmaf(omc, f[i], fmaf(om, ei, hf * si));
-                oo = fmaf(omc, f[o], fmaf(om, eo, hf * so));
-            } else {
-                const float fp = 0.5f * (f[i] + f[o]), fm = 0.5f * (f[i] - f[o]);
-                const float ep = 0.5f * (ei + eo), em = 0.5f * (ei - eo);
-                const float sp = 0.5f * (si + so), sm = 0.5f * (si - so);
-                const float even = hf * sp - om * (fp - ep), odd = hfm * sm - omm * (fm - em);
-                oi = f[i] + even + odd;
-                oo = f[o] + even - odd;
-            }
-            dsum += (f[i] - oi) + (f[o] - oo);
-            dk[(uint32_t)i * PS] = oi;
-            dk[(uint32_t)o * PS] = oo;
+            for (int i = 0; i < Q; ++i) dst0[e[opp<L>(i)]] = f[i];
+            continue;
         }
-        dk[0] = f[0] + dsum;  // mass balance
+        float* const dk = dst0 + kd;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dk[(uint32_t)i * PS] = f[i];
         if (OBS) {
             // stored post-collision momentum: j + F
-            const float pux = (jx + F) * irho, puy = jy * irho, puz = (L::D == 3) ? jz * irho : 0.f;
+            const float pux = __fmul_rn(__fadd_rn(jx, F), irho), puy = __fmul_rn(jy, irho),
+                        puz = (L::D == 3) ? __fmul_rn(jz, irho) : 0.f;
             const float px = uprev[kd], py = uprev[PS + kd];
             const float pz = (L::D == 3) ? uprev[2u * PS + kd] : 0.f;
             const float ex = pux - px, ey = puy - py, ez = puz - pz;
             const float uu = pux * pux + puy * puy + puz * puz;
-            a0s += jx + 0.5f * F;
+            a0s += fmaf(0.5f, F, jx);
             a1s += ex * ex + ey * ey + ez * ez;
             a2s += uu;
             umax2 = fmaxf(umax2, uu);
@@ -252,12 +285,65 @@ __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ H
     }
 }
 
+template <class L, int EQ, bool OBS>
+__global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ HotArgs A, const float* __restrict__ gforce,
+                                                      float* __restrict__ uprev, double* __restrict__ partials) {
+    periodic_strip<L, EQ, OBS, false>(A, gforce, uprev, partials);
+}
+template <class L, int EQ>
+__global__ void __launch_bounds__(128) k_periodic_gather(const __grid_constant__ HotArgs A,
+                                                        const float* __restrict__ gforce) {
+    periodic_strip<L, EQ, false, true>(A, gforce, nullptr, nullptr);
+}
+
+// Local step of the forced pair: each node's pre-collision f_j from its own
+// slot opp(j), post-collision f*_j to slot j; one lane per compact slot over
+// the local-step work items (slots between domains hold zero and stay zero:
+// no force acts there, they are never read as fluid).
+template <class L, int EQ>
+__global__ void __launch_bounds__(128) k_periodic_local(const __grid_constant__ HotArgs A,
+                                                       const float* __restrict__ gforce, uint32_t span) {
+    constexpr int Q = L::Q;
+    const int lane = threadIdx.x & 31;
+    const uint32_t witem = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (witem >= A.nvitems) return;
+    const uint2 it = __ldg(A.vitems + witem);
+    const DomainDev D = A.dom[it.y];
+    if (!D.active) return;
+    const uint32_t PS = A.pstride;
+    const float F = __fmul_rn(gforce[it.y], D.rho0);
+    float* const g = A.dst[0];  // a work item covers `span` slots, one per lane and pass
+#pragma unroll 1
+    for (uint32_t k = it.x + (uint32_t)lane; k < it.x + span; k += 32u) {
+        if (k >= D.fluid_end) return;
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = g[(uint32_t)opp<L>(i) * PS + k];
+        float dr, jx, jy, jz, irho;
+        forced_relax<L, EQ>(f, D.rho0, F, D.omega, D.omega_m, dr, jx, jy, jz, irho);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[(uint32_t)i * PS + k] = f[i];
+    }
+}
+
 namespace {
 template <class L, int EQ>
 cudaError_t periodic_dispatch(bool obs, unsigned nb, int threads, const HotArgs& A, const float* gforce,
                               float* uprev, double* partials, cudaStream_t st) {
     if (obs) k_periodic_step<L, EQ, true><<<nb, threads, 0, st>>>(A, gforce, uprev, partials);
     else k_periodic_step<L, EQ, false><<<nb, threads, 0, st>>>(A, gforce, uprev, partials);
+    return cudaGetLastError();
+}
+template <class L, int EQ>
+cudaError_t periodic_pair_dispatch(int half, const HotArgs& A, const float* gforce, cudaStream_t st) {
+    constexpr int threads = 128;
+    if (half == 0) {
+        const unsigned nb = (A.nitems + (threads / 32) - 1) / (threads / 32);
+        if (nb) k_periodic_gather<L, EQ><<<nb, threads, 0, st>>>(A, gforce);
+    } else {
+        const unsigned nb = (A.nvitems + (threads / 32) - 1) / (threads / 32);
+        if (nb) k_periodic_local<L, EQ><<<nb, threads, 0, st>>>(A, gforce, 32u * (uint32_t)local_step_vector(L::Q));
+    }
     return cudaGetLastError();
 }
 }  // namespace
@@ -276,6 +362,18 @@ cudaError_t launch_periodic_step(int q, int eq, bool obs, HotArgs A, const float
                        : periodic_dispatch<D2Q9, 1>(obs, nb, threads, A, gforce, uprev, partials, st);
     return eq == 0 ? periodic_dispatch<D3Q19, 0>(obs, nb, threads, A, gforce, uprev, partials, st)
                    : periodic_dispatch<D3Q19, 1>(obs, nb, threads, A, gforce, uprev, partials, st);
+}
+
+cudaError_t launch_periodic_half(int q, int eq, int half, HotArgs A, const float* gforce, float* g, cudaStream_t st) {
+    for (int i = 0; i < 19; ++i) {
+        A.src[i] = i < q ? g + (size_t)i * A.pstride : nullptr;
+        A.dst[i] = A.src[i] ? g + (size_t)i * A.pstride : nullptr;
+    }
+    if (q == 9)
+        return eq == 0 ? periodic_pair_dispatch<D2Q9, 0>(half, A, gforce, st)
+                       : periodic_pair_dispatch<D2Q9, 1>(half, A, gforce, st);
+    return eq == 0 ? periodic_pair_dispatch<D3Q19, 0>(half, A, gforce, st)
+                   : periodic_pair_dispatch<D3Q19, 1>(half, A, gforce, st);
 }
 
 }  // namespace lbmgb

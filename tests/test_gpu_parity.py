@@ -574,23 +574,60 @@ def _forced_masks():
     return [(9, m2), (19, m3)]
 
 
+@pytest.mark.parametrize("pairs", [True, False])
 @pytest.mark.parametrize("eq", [0, 1])
-def test_forced_periodic_steps_match_oracle(eq):
-    """Pull steps with periodic wrap in x, y (and z), halfway bounce-back and
-    Guo forcing, against the oracle from the rest start and a random state."""
+def test_forced_periodic_steps_match_oracle(eq, pairs):
+    """Steps with periodic wrap in x, y (and z), halfway bounce-back and Guo
+    forcing -- in-place pairs of the forced gather and local steps, or pull
+    steps -- against the oracle from the rest start and a random state."""
     rng = np.random.default_rng(7)
     tau, g = 0.8, 2e-4
     for q, mask in _forced_masks():
-        with lbm.lbm_batch_create_forced([mask], [tau], [g], lbm.make_options(equilibrium=eq)) as s:
+        with lbm.lbm_batch_create_forced([mask], [tau], [g], lbm.make_options(equilibrium=eq,
+                                                                               in_place_pairs=pairs)) as s:
             f0 = lbm.lbm_get_populations(s, 0)
-            lbm.lbm_step(s, 7)
-            _assert_close(lbm.lbm_get_populations(s, 0), O.run_forced(mask, f0, tau, g, 7, eq), q, mask)
+            lbm.lbm_step(s, 8)
+            _assert_close(lbm.lbm_get_populations(s, 0), O.run_forced(mask, f0, tau, g, 8, eq), q, mask)
             f = _w(q) * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
             f[mask.astype(bool)] = 0
             lbm.lbm_set_populations(s, 0, f)
             start = lbm.lbm_get_populations(s, 0)
             lbm.lbm_step(s, 1)
             _assert_close(lbm.lbm_get_populations(s, 0), O.step_forced(mask, start, tau, g, eq), q, mask)
+
+
+@pytest.mark.parametrize("coll", [0, 1])
+def test_forced_pairs_match_forced_pull_steps_bitwise(coll):
+    """The forced in-place pair (gather step writing each result back to the
+    slot it read -- periodic streaming and bounce-back keep the pairing exact
+    -- then the local step) relaxes every node with the same written-out
+    operations as the forced pull step: bit-identical populations and
+    observables from a random state, BGK and TRT, both equilibria, 2D and 3D,
+    for even and odd step counts."""
+    rng = np.random.default_rng(71 + coll)
+    for eq in (0, 1):
+        for q, mask in _forced_masks():
+            f = _w(q) * (1 + 0.05 * rng.standard_normal(mask.shape + (q,)))
+            f[mask.astype(bool)] = 0
+            out = {}
+            for pairs in (True, False):
+                opts = lbm.make_options(equilibrium=eq, in_place_pairs=pairs, collision=coll)
+                with lbm.lbm_batch_create_forced([mask, mask[..., ::-1].copy()], [0.7, 1.1], [3e-4, 1e-4],
+                                                 opts) as s:
+                    lbm.lbm_set_populations(s, 0, f)
+                    res = []
+                    for n in (2, 1, 6):
+                        lbm.lbm_step(s, n)
+                        res.append([lbm.lbm_get_populations(s, d) for d in range(2)])
+                    res.append(lbm.lbm_step_observe(s, 4))
+                    res.append([lbm.lbm_get_populations(s, d) for d in range(2)])
+                    out[pairs] = res
+            for a, b in zip(out[True], out[False]):
+                if isinstance(a, list):
+                    for x, y in zip(a, b):
+                        assert np.array_equal(x, y), (eq, q, coll)
+                else:
+                    assert np.array_equal(a, b), (eq, q, coll)
 
 
 def test_forced_permeability_matches_oracle_and_translation():
