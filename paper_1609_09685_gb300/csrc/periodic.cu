@@ -131,6 +131,36 @@ __device__ __forceinline__ uint32_t psrc(const PWin (&w)[L::NROW], const uint32_
     }
     return sf ? (uint32_t)I * PS + idx : (uint32_t)opp<L>(I) * PS + kd;
 }
+// The lanes at x = 0 (wrapl) and x = N_x - 1 (wrapr) take the x neighbour of
+// their c_x = +1 (resp. -1) directions from the other end of each source row:
+// that row's end segment gives its fluid flag and compact slot.  Applied
+// after the interior rule for the two lanes only.
+template <class L, int I>
+__device__ __forceinline__ void pwrap(uint32_t& e, const SegWindow* wdom, int y, int z, int ny, int nz, int nseg,
+                                      int lastl, bool wrapl, bool wrapr, uint32_t kd, uint32_t PS) {
+    constexpr int cx = L::c(I, 0);
+    if constexpr (cx != 0) {
+        if ((cx > 0 && wrapl) || (cx < 0 && wrapr)) {
+            const int yy = (y - L::c(I, 1) + ny) % ny, zz = (z - L::c(I, 2) + nz) % nz;
+            const uint4 r = __ldg(wdom + ((uint32_t)zz * ny + (uint32_t)yy) * nseg + (cx > 0 ? nseg - 1 : 0));
+            uint32_t fl, ix;
+            if (cx > 0) {  // node N_x - 1 of the source row: lane lastl of its last segment
+                fl = (r.w >> lastl) & 1u;
+                ix = r.z + (r.x & 1u) + __popc(r.w & ((1u << lastl) - 1u));
+            } else {  // node 0 of the source row: lane 0 of its first segment
+                fl = r.w & 1u;
+                ix = r.z + (r.x & 1u);
+            }
+            e = fl ? (uint32_t)I * PS + ix : (uint32_t)opp<L>(I) * PS + kd;
+        }
+    }
+}
+template <class L, int... Is>
+__device__ __forceinline__ void pwraps(uint32_t (&e)[L::Q], const SegWindow* wdom, int y, int z, int ny, int nz,
+                                       int nseg, int lastl, bool wrapl, bool wrapr, uint32_t kd, uint32_t PS,
+                                       std::integer_sequence<int, Is...>) {
+    (pwrap<L, Is>(e[Is], wdom, y, z, ny, nz, nseg, lastl, wrapl, wrapr, kd, PS), ...);
+}
 template <class L, int... Is>
 __device__ __forceinline__ void psrcs(uint32_t (&e)[L::Q], const PWin (&w)[L::NROW], const uint32_t (&fl_l)[L::NROW],
                                       const uint32_t (&ix_l)[L::NROW], const uint32_t (&fl_r)[L::NROW],
@@ -151,39 +181,6 @@ __device__ __forceinline__ float pwarp_max(float v) {
 }
 
 }  // namespace
-
-// Neighbour windows of row (y, z) for the lane: the windows of the source rows
-// (rows and planes wrap) and, for the lanes at x = 0 and x = N_x - 1, the fluid
-// flag and compact slot of their x neighbour at the other end of each source
-// row (from that row's end segment).
-template <class L>
-struct PRow {
-    PWin w[L::NROW];
-    uint32_t fl_l[L::NROW], ix_l[L::NROW], fl_r[L::NROW], ix_r[L::NROW];
-};
-template <class L>
-__device__ __forceinline__ void prow(PRow<L>& R, const SegWindow* wdom, int y, int z, int s, int ny, int nz,
-                                     int nseg, int lastl, bool wrapl, bool wrapr, int lane, uint32_t lmask) {
-    constexpr int NZ = (L::NROW == 9) ? 3 : 1;
-    auto rec = [&](int zz, int yy, int ss) { return __ldg(wdom + ((uint32_t)zz * ny + (uint32_t)yy) * nseg + ss); };
-#pragma unroll
-    for (int q = 0; q < L::NROW; ++q) {
-        const int dy = q % 3 - 1, dz = (NZ == 3) ? q / 3 - 1 : 0;
-        const int yy = (y + dy + ny) % ny, zz = (z + dz + nz) % nz;
-        R.w[q] = pwin(rec(zz, yy, s), lane, lmask);
-        R.fl_l[q] = R.ix_l[q] = R.fl_r[q] = R.ix_r[q] = 0u;
-        if (wrapl) {  // node N_x - 1 of the source row: lane lastl of its last segment
-            const uint4 e = rec(zz, yy, nseg - 1);
-            R.fl_l[q] = (e.w >> lastl) & 1u;
-            R.ix_l[q] = e.z + (e.x & 1u) + __popc(e.w & ((1u << lastl) - 1u));
-        }
-        if (wrapr) {  // node 0 of the source row: lane 0 of its first segment
-            const uint4 e = rec(zz, yy, 0);
-            R.fl_r[q] = e.w & 1u;
-            R.ix_r[q] = e.z + (e.x & 1u);
-        }
-    }
-}
 
 // Pull step (OBS: the observing variant) and the gather step of an in-place
 // pair (GATHER: each result written back to the slot it was read from, the
@@ -222,13 +219,23 @@ __device__ __forceinline__ void periodic_strip(const HotArgs& A, const float* __
 #pragma unroll 1
     for (int r = 0; r < nrows; ++r) {
         const int y = y0 + r;
-        PRow<L> R;
-        prow<L>(R, wdom, y, z, s, ny, nz, nseg, lastl, wrapl, wrapr, lane, lmask);
+        PWin w[L::NROW];
+#pragma unroll
+        for (int q = 0; q < L::NROW; ++q) {
+            const int dy = q % 3 - 1, dz = (L::NROW == 9) ? q / 3 - 1 : 0;
+            const int yy = (y + dy + ny) % ny, zz = (z + dz + nz) % nz;
+            w[q] = pwin(__ldg(wdom + ((uint32_t)zz * ny + (uint32_t)yy) * nseg + s), lane, lmask);
+        }
         constexpr int C = (L::NROW == 9) ? 4 : 1;
-        const bool fl = (R.w[C].tri >> 1) & 1u;
-        const uint32_t kd = R.w[C].i0 + (R.w[C].tri & 1u);
+        const bool fl = (w[C].tri >> 1) & 1u;
+        const uint32_t kd = w[C].i0 + (w[C].tri & 1u);
         uint32_t e[Q];
-        psrcs<L>(e, R.w, R.fl_l, R.ix_l, R.fl_r, R.ix_r, wrapl, wrapr, kd, PS, std::make_integer_sequence<int, Q>{});
+        {
+            const uint32_t zero[L::NROW] = {};
+            psrcs<L>(e, w, zero, zero, zero, zero, false, false, kd, PS, std::make_integer_sequence<int, Q>{});
+        }
+        if (wrapl || wrapr)
+            pwraps<L>(e, wdom, y, z, ny, nz, nseg, lastl, wrapl, wrapr, kd, PS, std::make_integer_sequence<int, Q>{});
         float f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = src[e[i]];
@@ -285,13 +292,21 @@ __device__ __forceinline__ void periodic_strip(const HotArgs& A, const float* __
     }
 }
 
+// Minimum resident 128-thread blocks per SM of the forced pair kernels, which
+// caps their registers: gather / local step in 2D (no spills at 6) and 3D
+// (the gather step fits 5 without spilling; the local step stays uncapped,
+// at 4, where it does not spill).
+template <class L, int HALF>
+struct PeriodicMinB {
+    static constexpr int value = L::Q == 9 ? 6 : (HALF == 0 ? 5 : 1);
+};
 template <class L, int EQ, bool OBS>
 __global__ void __launch_bounds__(128) k_periodic_step(const __grid_constant__ HotArgs A, const float* __restrict__ gforce,
                                                       float* __restrict__ uprev, double* __restrict__ partials) {
     periodic_strip<L, EQ, OBS, false>(A, gforce, uprev, partials);
 }
 template <class L, int EQ>
-__global__ void __launch_bounds__(128) k_periodic_gather(const __grid_constant__ HotArgs A,
+__global__ void __launch_bounds__(128, (PeriodicMinB<L, 0>::value)) k_periodic_gather(const __grid_constant__ HotArgs A,
                                                         const float* __restrict__ gforce) {
     periodic_strip<L, EQ, false, true>(A, gforce, nullptr, nullptr);
 }
@@ -301,7 +316,7 @@ __global__ void __launch_bounds__(128) k_periodic_gather(const __grid_constant__
 // the local-step work items (slots between domains hold zero and stay zero:
 // no force acts there, they are never read as fluid).
 template <class L, int EQ>
-__global__ void __launch_bounds__(128) k_periodic_local(const __grid_constant__ HotArgs A,
+__global__ void __launch_bounds__(128, (PeriodicMinB<L, 1>::value)) k_periodic_local(const __grid_constant__ HotArgs A,
                                                        const float* __restrict__ gforce, uint32_t span) {
     constexpr int Q = L::Q;
     const int lane = threadIdx.x & 31;

@@ -1,7 +1,8 @@
 """Launch configurations and the runtime autotuner, through the C ABI.
 
 Every launch configuration -- block size, strip rows, the direct gather
-step's row batch, the staged gather step's tile rows -- maps the same step
+step's row batch, the staged gather step's tile rows, the band gather step's
+band rows, the fused L2-blocked pair's block size -- maps the same step
 onto the GPU differently and must give bit-identical populations; the tuner
 picks among them by CUDA-event timing on the solver's stream and caches the
 choice per (device, lattice, size bucket, equilibrium, collision, kernel
@@ -37,7 +38,8 @@ def _run(masks, taus, drhos, launch=None, tune=None, steps=(7, 10)):
         res = None
         if launch is not None:
             lbm.lbm_set_launch(s, **launch)
-            assert lbm.lbm_get_launch(s) == dict(launch, tile_rows=launch.get("tile_rows", 0))
+            want = dict(dict(tile_rows=0, band_rows=0, pair_block_mb=0), **launch)
+            assert lbm.lbm_get_launch(s) == want
         if tune is not None:
             res = lbm.lbm_autotune(s, tune, 8)
         for n in steps:
@@ -55,6 +57,9 @@ def test_every_launch_configuration_is_bit_identical(dim):
                for bt in (32, 64, 256) for sr in (1, 5, 16) for gb in (lo, hi)]
     if dim == 2:
         configs += [dict(block_threads=128, strip_rows=8, gather_batch=4, tile_rows=tr) for tr in (1, 2, 3, 4)]
+        configs += [dict(block_threads=128, strip_rows=8, gather_batch=4, band_rows=br) for br in (1, 7, 64)]
+    # fused pairs over blocks of 1 MB (several blocks on these masks only in 2D)
+    configs += [dict(block_threads=128, strip_rows=sr, gather_batch=hi, pair_block_mb=1) for sr in (4, 8)]
     for cfg in configs:
         got, _, _ = _run(masks, taus, drhos, launch=cfg)
         for a, b in zip(ref, got):
@@ -66,13 +71,18 @@ def test_launch_configuration_is_validated():
     with lbm.lbm_batch_create(masks, taus, drhos) as s:
         for bad in (dict(block_threads=48, strip_rows=8, gather_batch=4), dict(block_threads=128, strip_rows=0,
                     gather_batch=4), dict(block_threads=128, strip_rows=8, gather_batch=3),
-                    dict(block_threads=128, strip_rows=8, gather_batch=4, tile_rows=5)):
+                    dict(block_threads=128, strip_rows=8, gather_batch=4, tile_rows=5),
+                    dict(block_threads=128, strip_rows=8, gather_batch=4, band_rows=65),
+                    dict(block_threads=128, strip_rows=8, gather_batch=4, tile_rows=2, band_rows=8),
+                    dict(block_threads=128, strip_rows=8, gather_batch=4, pair_block_mb=5000)):
             with pytest.raises(lbm.LBMError):
                 lbm.lbm_set_launch(s, **bad)
     masks3, taus3, drhos3 = _batch(3)
     with lbm.lbm_batch_create(masks3, taus3, drhos3) as s:
         with pytest.raises(lbm.LBMError):  # no staged gather step for D3Q19
             lbm.lbm_set_launch(s, 128, 8, 2, 2)
+        with pytest.raises(lbm.LBMError):  # nor a band gather step
+            lbm.lbm_set_launch(s, 128, 8, 2, 0, 8)
 
 
 def test_time_steps_leaves_the_state_alone():
