@@ -194,6 +194,13 @@ __device__ __forceinline__ void aa_gather_body(const HotArgs& A) {
     }
 }
 
+// Window records staged per chunk of this many strip rows (a multiple of every
+// row batch), or (0) read from global memory row by row.
+#ifndef LBM_AA_WIN_STAGE
+#define LBM_AA_WIN_STAGE 1
+#endif
+constexpr int kWinRows = 32;
+
 // Gather step with the source slots parked in shared memory: a batch of RS
 // rows keeps only its loaded values in registers, so more rows of loads are in
 // flight per warp at the same register budget.
@@ -284,14 +291,40 @@ __device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item,
         pbase[zi] = (uint32_t)zz * (uint32_t)ny;
     }
     auto rowc = [&](int yy) { return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy); };
+    // Window records of a chunk of kWinRows rows (and the rows on either
+    // side, in every plane the strip pulls from), staged in shared memory by
+    // one load per lane, so that a batch's source loads do not wait on its
+    // own window loads.  rw(zi, y) = the window of row y (clamped) in plane zi.
+    constexpr int KW = kWinRows;
+    const uint4* const wst = reinterpret_cast<const uint4*>(sme + (size_t)(blockDim.x >> 5) * RS * Q * 32) +
+                             (size_t)wid * NZ * (KW + 2);
+    auto stage = [&](int c) {  // rows y0 + c - 1 .. of the chunk starting at strip row c
+        __syncwarp();
+        const int nr = min(KW, nrows - c) + 2;
+        uint4* const dst = const_cast<uint4*>(wst);
+        for (int t = lane; t < NZ * nr; t += 32) {
+            const int zi = t / nr, r = t - zi * nr;
+            int zz = z + zi - (NZ == 3 ? 1 : 0);  // (not pbase[zi]: a runtime index would put it in local memory)
+            zz = zz < 0 ? 0 : (zz >= D.nz ? D.nz - 1 : zz);
+            dst[zi * (KW + 2) + r] = __ldg(wcol + ((uint32_t)zz * (uint32_t)ny + rowc(y0 + c - 1 + r)) * rs);
+        }
+        __syncwarp();
+    };
+    if (LBM_AA_WIN_STAGE) stage(0);
+    // window of row y in plane zi; ybase = y0 + (first strip row of the staged chunk) - 1
+    auto win_of = [&](int zi, int y, int ybase) {
+        return LBM_AA_WIN_STAGE ? wst[zi * (KW + 2) + (y - ybase)] : __ldg(wcol + (pbase[zi] + rowc(y)) * rs);
+    };
     constexpr bool kSlide = (NZ == 1);
     Win wm, wc, wp;
     if (kSlide) {
-        wm = make_win(__ldg(wcol + (pbase[0] + rowc(y0 - 1)) * rs), lane, lmask);
-        wc = make_win(__ldg(wcol + (pbase[0] + y0) * rs), lane, lmask);
+        wm = make_win(win_of(0, y0 - 1, y0 - 1), lane, lmask);
+        wc = make_win(win_of(0, y0, y0 - 1), lane, lmask);
     }
 #pragma unroll 1
     for (int r0 = 0; r0 < nrows; r0 += RS) {
+        if (LBM_AA_WIN_STAGE && r0 > 0 && r0 % KW == 0) stage(r0);
+        const int ybase = y0 + (r0 / KW) * KW - 1;
         float f[RS][Q];
         uint32_t flb = 0u;
 #pragma unroll
@@ -301,7 +334,7 @@ __device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item,
             const int y = y0 + min(r0 + j, nrows - 1);
             Win w[L::NROW];
             if (kSlide) {
-                wp = make_win(__ldg(wcol + (pbase[0] + rowc(y + 1)) * rs), lane, lmask);
+                wp = make_win(win_of(0, y + 1, ybase), lane, lmask);
                 w[0] = wm;
                 w[1] = wc;
                 w[2] = wp;
@@ -313,7 +346,7 @@ __device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item,
 #pragma unroll
                 for (int q = 0; q < L::NROW; ++q) {
                     const int zi = q / 3, dy = q % 3 - 1;
-                    w[q] = make_win(__ldg(wcol + (pbase[zi] + rowc(y + dy)) * rs), lane, lmask);
+                    w[q] = make_win(win_of(zi, y + dy, ybase), lane, lmask);
                 }
             }
             constexpr int C = (L::NROW == 9) ? 4 : 1;
@@ -351,7 +384,10 @@ __device__ __forceinline__ void aa_gather_smem_body(const HotArgs& A) {
 }
 template <class L>
 constexpr size_t gather_smem_bytes(int threads, int rs) {
-    return GatherSmem<L>::on ? (size_t)(threads / 32) * (size_t)rs * L::Q * 32 * sizeof(uint32_t) : 0;
+    constexpr int NZ = (L::NROW == 9) ? 3 : 1;
+    return GatherSmem<L>::on ? (size_t)(threads / 32) * ((size_t)rs * L::Q * 32 * sizeof(uint32_t) +
+                                                         (LBM_AA_WIN_STAGE ? (size_t)NZ * (kWinRows + 2) * 16 : 0))
+                             : 0;
 }
 
 // RS: rows of loads a warp keeps in flight (the "gather batch" of a launch
