@@ -200,6 +200,13 @@ __device__ __forceinline__ void aa_gather_body(const HotArgs& A) {
 #define LBM_AA_WIN_STAGE 1
 #endif
 constexpr int kWinRows = 32;
+// D3Q19: slide the windows down the strip as in 2D (1) or take all nine per
+// row from the staged chunk (0, the default: sliding keeps six more windows
+// live, spills at the register cap and measured 480 vs 429 us per launch on
+// four 256x128x128 domains).
+#ifndef LBM_AA_SLIDE_3D
+#define LBM_AA_SLIDE_3D 0
+#endif
 
 // Gather step with the source slots parked in shared memory: a batch of RS
 // rows keeps only its loaded values in registers, so more rows of loads are in
@@ -315,11 +322,16 @@ __device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item,
     auto win_of = [&](int zi, int y, int ybase) {
         return LBM_AA_WIN_STAGE ? wst[zi * (KW + 2) + (y - ybase)] : __ldg(wcol + (pbase[zi] + rowc(y)) * rs);
     };
-    constexpr bool kSlide = (NZ == 1);
-    Win wm, wc, wp;
+    // 2D (and 3D with LBM_AA_SLIDE_3D): windows slide down the strip, rows
+    // y - 1 and y of every plane carry over and only row y + 1 is read per row
+    constexpr bool kSlide = (NZ == 1) || LBM_AA_SLIDE_3D;
+    Win wm[NZ], wc[NZ], wp[NZ];
     if (kSlide) {
-        wm = make_win(win_of(0, y0 - 1, y0 - 1), lane, lmask);
-        wc = make_win(win_of(0, y0, y0 - 1), lane, lmask);
+#pragma unroll
+        for (int zi = 0; zi < NZ; ++zi) {
+            wm[zi] = make_win(win_of(zi, y0 - 1, y0 - 1), lane, lmask);
+            wc[zi] = make_win(win_of(zi, y0, y0 - 1), lane, lmask);
+        }
     }
 #pragma unroll 1
     for (int r0 = 0; r0 < nrows; r0 += RS) {
@@ -334,13 +346,16 @@ __device__ __forceinline__ void aa_gather_strip(const HotArgs& A, uint32_t item,
             const int y = y0 + min(r0 + j, nrows - 1);
             Win w[L::NROW];
             if (kSlide) {
-                wp = make_win(win_of(0, y + 1, ybase), lane, lmask);
-                w[0] = wm;
-                w[1] = wc;
-                w[2] = wp;
-                if (r0 + j + 1 < nrows) {
-                    wm = wc;
-                    wc = wp;
+#pragma unroll
+                for (int zi = 0; zi < NZ; ++zi) {
+                    wp[zi] = make_win(win_of(zi, y + 1, ybase), lane, lmask);
+                    w[3 * zi] = wm[zi];
+                    w[3 * zi + 1] = wc[zi];
+                    w[3 * zi + 2] = wp[zi];
+                    if (r0 + j + 1 < nrows) {
+                        wm[zi] = wc[zi];
+                        wc[zi] = wp[zi];
+                    }
                 }
             } else {
 #pragma unroll
