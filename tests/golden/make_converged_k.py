@@ -17,7 +17,7 @@ Sets (names as in the tests):
       seed 2026), master seed 2026
   C4  256x128x128 D3Q19, porosity 0.70, tau 0.52 and 0.6
 
-    python tests/golden/make_converged_k.py [--sets C1,C2,C3] [--procs N] [--names A,B] [--maxiter M]
+    python tests/golden/make_converged_k.py [--sets C1,C2,C3] [--procs N] [--names A,B] [--maxiter M] [--inner I]
     python tests/golden/make_converged_k.py --merge-only
 
 Runs one process per job (spawned), longest first.  Each result is saved as
@@ -80,6 +80,7 @@ def cost(d):
 
 
 MAXITER = 400
+INNER = 30
 
 
 def solve(job):
@@ -87,10 +88,11 @@ def solve(job):
     from oracle import steady
     set_name, name, d = job[:3]
     maxiter = job[3] if len(job) > 3 else MAXITER
+    inner = job[4] if len(job) > 4 else INNER
     t0 = time.time()
     mask, _ = O.qsgs(d.shape, d.seed, d.core_p, d.porosity, d.d_face)
     perc = O.percolates(mask)
-    f, info = steady.steady_state(mask, d.tau, 1.0 + d.drho, 1.0, maxiter=maxiter)
+    f, info = steady.steady_state(mask, d.tau, 1.0 + d.drho, 1.0, maxiter=maxiter, inner_maxiter=inner)
     k = O.permeability(mask, f, d.tau, 1.0 + d.drho, 1.0)
     fields = O.fields(mask, f)
     fl = np.flatnonzero(mask.ravel() == 0)
@@ -161,6 +163,7 @@ def main():
     ap.add_argument("--procs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--names", default="", help="only these domains (comma list), e.g. to re-solve one")
     ap.add_argument("--maxiter", type=int, default=MAXITER, help="Newton iterations of the root finder")
+    ap.add_argument("--inner", type=int, default=INNER, help="inner (LGMRES) iterations per Newton step")
     ap.add_argument("--merge-only", action="store_true", help="only merge the saved results into the final files")
     a = ap.parse_args()
     if a.merge_only:
@@ -170,7 +173,7 @@ def main():
     if a.names:
         keep = set(a.names.split(","))
         todo = [j for j in todo if j[1] in keep]
-    todo = [j + (a.maxiter,) for j in todo]
+    todo = [j + (a.maxiter, a.inner) for j in todo]
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool, open(PARTIAL, "a") as part:
         for r in pool.imap_unordered(solve, todo):
