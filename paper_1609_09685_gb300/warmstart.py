@@ -244,9 +244,12 @@ def make_domains(n: int, shape, seed0: int, porosity=(0.6, 0.8), tau=(0.51, 1.5)
     return out
 
 
-def generate(domains, shape, stream=None, max_steps: int = 400_000, tol: float = 1e-9, core_p: float = 0.02):
-    """Solve every domain to steady state with the batched solver and keep
-    masks, network inputs and normalised targets on the device."""
+def generate(domains, shape, stream=None, max_steps: int = 400_000, tol: float = 1e-9, core_p: float = 0.02,
+             chunk: int = 2048):
+    """Solve every domain to steady state with the batched solver (in
+    batches of at most `chunk` domains: a batch's Q x nodes must stay below
+    2^32) and keep masks, network inputs and normalised targets on the
+    device."""
     torch = _torch()
     h, w = shape
     ds = Dataset(h, w)
@@ -259,14 +262,16 @@ def generate(domains, shape, stream=None, max_steps: int = 400_000, tol: float =
     ds.masks_host = masks
     n = len(masks)
     t0 = time.perf_counter()
-    s = lbm.lbm_batch_create(masks, ds.taus, ds.drhos, lbm.make_options(stream=stream))
-    _, st, steps, _ = lbm.lbm_run_to_steady(s, tol, max_steps)
-    ds.steps = [int(v) for v in steps]
     ds.targets = torch.empty((n, h, w, N_TARGET), dtype=torch.float32, device="cuda")
-    for d in range(n):
-        lbm.lbm_nn_targets(s, d, ds.targets[d])
-    torch.cuda.synchronize()
-    s.close()
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        s = lbm.lbm_batch_create(masks[c0:c1], ds.taus[c0:c1], ds.drhos[c0:c1], lbm.make_options(stream=stream))
+        _, st, steps, _ = lbm.lbm_run_to_steady(s, tol, max_steps)
+        ds.steps += [int(v) for v in steps]
+        for d in range(c1 - c0):
+            lbm.lbm_nn_targets(s, d, ds.targets[c0 + d])
+        torch.cuda.synchronize()
+        s.close()
     ds.seconds = time.perf_counter() - t0
     ds.solid = torch.from_numpy(np.stack(masks)).to("cuda")
     ds.inputs = torch.empty((n, h, w, C_IN), dtype=torch.bfloat16, device="cuda")
