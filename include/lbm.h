@@ -108,17 +108,18 @@ typedef struct lbm_options {
     void (*free_fn)(void* ctx, void* ptr, void* stream);
     void* alloc_ctx;
     int32_t band_rows;       /* gather step of the in-place pair (D2Q9): 1..64 = band gather step -- a block walks
-                                down up to this many rows of a piece of up to 512 nodes of the width, staging
-                                each row's compact range of every plane in a shared-memory ring by bulk copies
-                                (one copy per plane and row) -- ; -1 = not used; 0 = the library's default.
-                                Ignored with tile_rows > 0 (both > 0 is an error), for D3Q19 and for
-                                force-driven or slab solvers.  Bit-identical results either way. */
+                                down up to this many rows of a piece of up to 256 nodes (8 segments) of the
+                                width, staging each row's compact range of every plane in a shared-memory ring
+                                by bulk copies (one copy per plane and row) -- ; -1 = not used; 0 = the
+                                library's default (not used: the direct gather step measured faster).  Both
+                                band_rows and tile_rows > 0 is an error; ignored for D3Q19 and for force-driven
+                                or slab solvers.  Bit-identical results either way. */
     int32_t pair_block_mb;   /* L2-blocked pairs (1..4096): both steps of an in-place pair in one persistent
                                 launch over blocks of about this many MB of populations -- the gather step runs
                                 about 32 MB of blocks ahead of the local step, which then reads each block
                                 while it is still in L2 -- instead of two whole-batch launches; -1 = whole-batch
-                                pairs; 0 = the library's default.  Used with the direct gather step only.
-                                Bit-identical results either way. */
+                                pairs; 0 = the library's default (whole-batch pairs, measured faster).  Used with
+                                the direct gather step only.  Bit-identical results either way. */
 } lbm_options;
 
 /* One domain of a batch. */
