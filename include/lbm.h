@@ -54,7 +54,9 @@ typedef enum {
     LBM_DIVERGED = -4, /* a non-finite velocity appeared */
     LBM_TIMEOUT = -5,
     LBM_ERR_IO = -6,
-    LBM_ERR_INTERNAL = -7,
+    LBM_ERR_INTERNAL = -7, /* a kernel's bounded wait gave up (a staged or band gather step's copy, a fused
+                              pair's wait on its neighbouring blocks), or a checked build met an out-of-range
+                              index; reported at the next observation from the device error word */
     LBM_CANCELLED = -8
 } lbm_status;
 
