@@ -7,10 +7,11 @@ the oracle's own steady states -- fixed points of its FP64 step -- on:
   C1  the 100x50 domains of seeds 1-10 (tau 0.8, rho_in/rho_out 1.0005/1);
   C2  all 24 domains of the Sec. 2 tau sweep (400x200 ... 1200x600);
   C3  16 of the 128 uneven batch domains;
-  C4  the 256x128x128 D3Q19 domain at tau 0.52 and 0.6.
+  C4  the 256x128x128 D3Q19 domain at tau 0.6 (when stored: its oracle
+      solve takes longer than a working day of one core).
 Each set runs on the GPU as one batch in the default launch configuration
 (the one bench.py times), from the solver's own initial state, iterated by
-lbm_run_to_steady (residual 1e-9).  C2-C4 run until the FP32 state stops
+lbm_run_to_steady (residual 1e-9).  C2, C3 (and C4) run until the FP32 state stops
 changing: the k-based stop at k_tol = 1e-7 and the stall rule over 2000
 checks (2e5 steps), or 8e6 steps.  The library's defaults (k_tol 1e-5, 200
 checks) stop earlier: they already give k within 1e-4 there, but on the
